@@ -1,0 +1,154 @@
+/*
+ * onesweep.h - C ABI of the GB300 Onesweep LSD radix sort.
+ *
+ * Implements the sort of Adinets and Merrill, "Onesweep: A Faster Least
+ * Significant Digit Radix Sort for GPUs" (arXiv 2206.01784):
+ *   phase 1  one pass computes the digit histograms of every digit place
+ *            (Section 3, "Upfront histogram kernel"; Figure 5);
+ *   phase 2  an exclusive prefix sum of each histogram gives the global bin
+ *            offsets (Section 3, "Exclusive sum kernel");
+ *   phase 3  p single-pass chained-scan digit-binning passes, least
+ *            significant place first (Section 3, "Chained scan digit-binning
+ *            kernel"; Figures 6-8).
+ * The problem solved is the paper's: an ascending, stable sort of keys held in
+ * GPU global memory, optionally carrying 32-bit payload values (Section 1;
+ * Section 4 evaluates 32/64-bit keys and 32-bit values).
+ *
+ * Conventions shared by every call:
+ *  - Pointers named *_in / *_out / ws are DEVICE pointers; the caller owns all
+ *    of them. The library never allocates device memory: scratch space is the
+ *    caller's workspace `ws` of at least os_sort_workspace_bytes() bytes.
+ *  - Keys are raw bit patterns: uint32 (OS_KEY_U32), uint64 (OS_KEY_U64),
+ *    IEEE-754 binary32 (OS_KEY_F32) or binary64 (OS_KEY_F64). Float keys are
+ *    ordered through the bijective sign-flip (negative keys: all bits
+ *    inverted; others: sign bit set), so -0.0 sorts before +0.0 and NaNs sort
+ *    by bit pattern (negative NaNs first, positive NaNs last). Output keys
+ *    carry the input bits unchanged.
+ *  - [begin_bit, end_bit) selects the key bits sorted on (of the sign-flipped
+ *    bits for float keys), 0 <= begin_bit <= end_bit <= key width. Digit
+ *    places are 8 bits wide, start at begin_bit and go upward; the last place
+ *    is narrower when the range is not a multiple of 8. begin_bit == end_bit
+ *    copies the input.
+ *  - Sorting is stable: equal keys keep their input order, and values follow
+ *    their keys.
+ *  - n must be below 2^30 (the chained scan keeps 30-bit counts, Section 3
+ *    "Handling very large problems"); larger n returns OS_ERR_TOO_LARGE.
+ *  - Inputs are never modified. Input, output and workspace ranges must not
+ *    overlap (OS_ERR_INVALID_ARG). Key pointers must be aligned to the key
+ *    width and value pointers to 4 bytes.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls only
+ *    enqueue work and return after host-side validation; results are ready
+ *    when the stream reaches them. Errors found on the device (a look-back
+ *    wait that ran past its limit) are reported by os_workspace_status().
+ *  - Calls that share a workspace must not overlap on the GPU.
+ */
+#ifndef ONESWEEP_H
+#define ONESWEEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define OS_API __attribute__((visibility("default")))
+#else
+#define OS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OS_KEY_U32 = 0,
+    OS_KEY_U64 = 1,
+    OS_KEY_F32 = 2,
+    OS_KEY_F64 = 3
+} os_key_type;
+
+typedef enum {
+    OS_OK = 0,
+    OS_ERR_INVALID_ARG = 1, /* bad key type, bit range, pointer, alignment or overlap */
+    OS_ERR_TOO_LARGE = 2,   /* n >= 2^30 */
+    OS_ERR_WORKSPACE = 3,   /* workspace missing or smaller than required */
+    OS_ERR_CUDA = 4,        /* a CUDA call or kernel launch failed */
+    OS_ERR_TIMEOUT = 5      /* a chained-scan look-back wait ran past its limit */
+} os_status;
+
+/* Where the parts of a sort's workspace sit (byte offsets from ws). */
+typedef struct {
+    size_t total_bytes;        /* what os_sort_workspace_bytes() returns */
+    size_t status_offset[2];   /* the two status-counter slabs (pass i uses slab i % 2) */
+    size_t histogram_offset;   /* uint32 [places][256] digit counts */
+    size_t bin_offset_offset;  /* uint32 [places][256] global bin offsets */
+    size_t alt_keys_offset;    /* ping-pong key buffer */
+    size_t alt_values_offset;  /* ping-pong value buffer (0 bytes for keys only) */
+    uint32_t tile_keys;        /* keys per binning tile */
+    uint32_t num_tiles;        /* tiles per binning pass */
+    uint32_t num_places;       /* p */
+} os_workspace_layout;
+
+/*
+ * Workspace bytes for sorting n keys of key_type over [begin_bit, end_bit)
+ * with value_bytes = 0 (keys only) or 4 (uint32 values). Returns 0 for
+ * invalid arguments. The workspace holds the digit histograms and bin offsets
+ * (Section 3, phases 1-2), two slabs of 32-bit status counters, one per
+ * (tile, digit) (Section 3, Figure 6), and the ping-pong key/value buffers.
+ */
+OS_API size_t os_sort_workspace_bytes(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_bit);
+
+/* Fills *layout for the same arguments. Returns OS_OK or OS_ERR_INVALID_ARG. */
+OS_API int os_sort_workspace_layout(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_bit,
+                             os_workspace_layout *layout);
+
+/*
+ * Sorts n keys (Section 3, all three phases). keys_in: n keys (device);
+ * keys_out: n keys (device), receives the stable ascending order. Returns an
+ * os_status.
+ */
+OS_API int os_sort_keys(int key_type, const void *keys_in, void *keys_out, uint64_t n, int begin_bit, int end_bit,
+                 void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Sorts n (key, uint32 value) pairs by key (Section 3; Section 4 sorts
+ * 32-bit keys with 32-bit values). vals_in / vals_out: n uint32 (device);
+ * each value moves with its key. Returns an os_status.
+ */
+OS_API int os_sort_pairs(int key_type, const void *keys_in, void *keys_out, const uint32_t *vals_in, uint32_t *vals_out,
+                  uint64_t n, int begin_bit, int end_bit, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Phases 1 and 2 only (Section 3, "Upfront histogram kernel" and
+ * "Exclusive sum kernel"): the digit counts of every place of the n keys and
+ * their exclusive prefix sums. hist_out and offsets_out are device arrays of
+ * uint32 [p][256] (either may be NULL). ws: a workspace sized by
+ * os_sort_workspace_bytes(key_type, n, 0, begin_bit, end_bit).
+ */
+OS_API int os_digit_histograms(int key_type, const void *keys_in, uint64_t n, int begin_bit, int end_bit,
+                        uint32_t *hist_out, uint32_t *offsets_out, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Waits for `stream`, then reports what the device recorded in the
+ * workspace's status word during the last call that used it: OS_OK,
+ * OS_ERR_TIMEOUT (a look-back wait gave up; the output is not valid) or
+ * OS_ERR_CUDA (the stream reported an error).
+ */
+OS_API int os_workspace_status(const void *ws, void *stream);
+
+/* A static, human-readable name for an os_status value. */
+OS_API const char *os_status_string(int status);
+
+/*
+ * Fault injection for tests of the look-back wait limit (not part of the
+ * method). With tile >= 0, every later binning pass skips all status-counter
+ * publishes of that tile, so the tiles after it wait until `spin_limit`
+ * polls have gone by, record OS_ERR_TIMEOUT and finish with invalid output.
+ * tile = -1 switches injection off; spin_limit = 0 restores the default
+ * limit. Process-wide setting, applied at launch time.
+ */
+OS_API void os_debug_set_lookback_fault(int64_t tile, uint32_t spin_limit);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ONESWEEP_H */

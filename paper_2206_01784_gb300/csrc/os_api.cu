@@ -1,0 +1,331 @@
+// Host driver and C ABI of the GB300 Onesweep sort (arXiv 2206.01784).
+//
+// Section 3, "High-level description": the sort is three phases, each a GPU
+// kernel - one histogram pass over all digit places, an exclusive sum of each
+// histogram, then p chained-scan digit-binning passes. Here phases 1 and 2
+// share one launch; the driver validates arguments, carves the caller's
+// workspace, zeroes its small header with one memset and enqueues the
+// launches on the caller's stream. Nothing is allocated and nothing waits on
+// the host.
+#include <cstdio>
+#include <cstring>
+
+#include "../../include/onesweep.h"
+#include "os_common.cuh"
+#include "os_internal.h"
+
+namespace onesweep {
+
+cudaError_t launch_binning32(bool pairs, const PassArgs& a, cudaStream_t s);
+cudaError_t launch_binning64(bool pairs, const PassArgs& a, cudaStream_t s);
+uint32_t binning_tile_keys32(bool pairs);
+uint32_t binning_tile_keys64(bool pairs);
+
+uint32_t binning_tile_keys(int key_bits, bool pairs) {
+  return key_bits == 32 ? binning_tile_keys32(pairs) : binning_tile_keys64(pairs);
+}
+
+cudaError_t launch_binning(int key_bits, bool pairs, const PassArgs& a, cudaStream_t s) {
+  return key_bits == 32 ? launch_binning32(pairs, a, s) : launch_binning64(pairs, a, s);
+}
+
+namespace {
+
+constexpr uint64_t kMaxKeys = 1ull << 30;     // 30-bit status counter values
+constexpr size_t kAlign = 256;
+constexpr uint32_t kDefaultSpinLimit = 1u << 22;
+
+// Header layout: word 0 device status, word 1 done counter of the histogram
+// kernel, words 16..23 tile counters of the binning passes.
+constexpr size_t kHeaderBytes = 256;
+constexpr size_t kDoneWord = 1;
+constexpr size_t kTileCounterWord = 16;
+
+int64_t g_fault_tile = -1;
+uint32_t g_spin_limit = kDefaultSpinLimit;
+
+size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int key_bits_of(int key_type) {
+  switch (key_type) {
+    case OS_KEY_U32:
+    case OS_KEY_F32: return 32;
+    case OS_KEY_U64:
+    case OS_KEY_F64: return 64;
+    default: return 0;
+  }
+}
+
+bool is_float(int key_type) { return key_type == OS_KEY_F32 || key_type == OS_KEY_F64; }
+
+struct Plan {
+  int key_bits = 0;
+  bool pairs = false;
+  int places = 0;
+  uint32_t tile = 0;
+  uint32_t tiles = 0;
+  os_workspace_layout layout{};
+};
+
+int make_plan(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_bit, Plan* plan) {
+  const int kb = key_bits_of(key_type);
+  if (kb == 0) return OS_ERR_INVALID_ARG;
+  if (value_bytes != 0 && value_bytes != 4) return OS_ERR_INVALID_ARG;
+  if (begin_bit < 0 || end_bit > kb || begin_bit > end_bit) return OS_ERR_INVALID_ARG;
+  if (n >= kMaxKeys) return OS_ERR_TOO_LARGE;
+  plan->key_bits = kb;
+  plan->pairs = value_bytes == 4;
+  plan->places = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
+  plan->tile = binning_tile_keys(kb, plan->pairs);
+  plan->tiles = (uint32_t)((n + plan->tile - 1) / plan->tile);
+  os_workspace_layout& L = plan->layout;
+  std::memset(&L, 0, sizeof(L));
+  size_t off = kHeaderBytes;
+  L.histogram_offset = off;
+  off = round_up(off + (size_t)8 * kRadix * 4);
+  L.bin_offset_offset = off;
+  off = round_up(off + (size_t)8 * kRadix * 4);
+  const size_t slab = (size_t)plan->tiles * kRadix * 4;
+  L.status_offset[0] = off;
+  off = round_up(off + slab);
+  L.status_offset[1] = off;
+  off = round_up(off + (plan->places > 1 ? slab : 0));
+  L.alt_keys_offset = off;
+  off = round_up(off + (plan->places > 1 ? (size_t)n * (kb / 8) : 0));
+  L.alt_values_offset = off;
+  off = round_up(off + (plan->places > 1 && plan->pairs ? (size_t)n * 4 : 0));
+  L.total_bytes = off;
+  L.tile_keys = plan->tile;
+  L.num_tiles = plan->tiles;
+  L.num_places = (uint32_t)plan->places;
+  return OS_OK;
+}
+
+bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
+  if (!a || !b || abytes == 0 || bbytes == 0) return false;
+  const char* x = static_cast<const char*>(a);
+  const char* y = static_cast<const char*>(b);
+  return x < y + bbytes && y < x + abytes;
+}
+
+int device_sm_count() {
+  static int cached_dev = -1, cached_sms = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (dev != cached_dev) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    cached_sms = sms;
+    cached_dev = dev;
+  }
+  return cached_sms;
+}
+
+// Phases 1 + 2 into the workspace (header already zeroed).
+int run_histogram(const Plan& plan, int key_type, const void* keys, uint64_t n, int begin_bit, int end_bit,
+                  char* ws, bool clear_slab0, cudaStream_t s) {
+  HistArgs h{};
+  h.keys = keys;
+  h.n = n;
+  h.flip = is_float(key_type);
+  h.num_places = plan.places;
+  h.begin_bit = begin_bit;
+  h.end_bit = end_bit;
+  h.hist = reinterpret_cast<uint32_t*>(ws + plan.layout.histogram_offset);
+  h.offsets = reinterpret_cast<uint32_t*>(ws + plan.layout.bin_offset_offset);
+  h.done_counter = reinterpret_cast<uint32_t*>(ws) + kDoneWord;
+  h.clear = clear_slab0 ? reinterpret_cast<uint32_t*>(ws + plan.layout.status_offset[0]) : nullptr;
+  h.clear_words = clear_slab0 ? (uint64_t)plan.tiles * kRadix : 0;
+  const int sms = device_sm_count();
+  if (sms <= 0) return OS_ERR_CUDA;
+  return launch_histogram(plan.key_bits, h, sms, s) == cudaSuccess ? OS_OK : OS_ERR_CUDA;
+}
+
+int run_sort(int key_type, const void* keys_in, void* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
+             uint64_t n, int begin_bit, int end_bit, void* ws, size_t ws_bytes, void* stream) {
+  const bool pairs = vals_in != nullptr || vals_out != nullptr;
+  if (pairs && (vals_in == nullptr || vals_out == nullptr)) return OS_ERR_INVALID_ARG;
+  Plan plan;
+  int rc = make_plan(key_type, n, pairs ? 4 : 0, begin_bit, end_bit, &plan);
+  if (rc != OS_OK) return rc;
+  if (n == 0) return OS_OK;
+  const size_t kbytes = (size_t)n * (plan.key_bits / 8);
+  const size_t vbytes = pairs ? (size_t)n * 4 : 0;
+  if (!keys_in || !keys_out) return OS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(keys_in) % (plan.key_bits / 8) ||
+      reinterpret_cast<uintptr_t>(keys_out) % (plan.key_bits / 8))
+    return OS_ERR_INVALID_ARG;
+  if (pairs && (reinterpret_cast<uintptr_t>(vals_in) % 4 || reinterpret_cast<uintptr_t>(vals_out) % 4))
+    return OS_ERR_INVALID_ARG;
+  if (!ws || ws_bytes < plan.layout.total_bytes) return OS_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(ws) % 16) return OS_ERR_INVALID_ARG;
+  if (overlaps(keys_in, kbytes, keys_out, kbytes) || overlaps(keys_in, kbytes, ws, plan.layout.total_bytes) ||
+      overlaps(keys_out, kbytes, ws, plan.layout.total_bytes))
+    return OS_ERR_INVALID_ARG;
+  if (pairs) {
+    const void* bufs[4] = {keys_in, keys_out, vals_in, vals_out};
+    const size_t sizes[4] = {kbytes, kbytes, vbytes, vbytes};
+    for (int i = 0; i < 4; ++i)
+      for (int j = i + 1; j < 4; ++j)
+        if (overlaps(bufs[i], sizes[i], bufs[j], sizes[j])) return OS_ERR_INVALID_ARG;
+    if (overlaps(vals_in, vbytes, ws, plan.layout.total_bytes) ||
+        overlaps(vals_out, vbytes, ws, plan.layout.total_bytes))
+      return OS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+
+  if (plan.places == 0) {  // empty bit range: a plain copy
+    if (cudaMemsetAsync(w, 0, 4, s) != cudaSuccess) return OS_ERR_CUDA;
+    if (cudaMemcpyAsync(keys_out, keys_in, kbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return OS_ERR_CUDA;
+    if (pairs && cudaMemcpyAsync(vals_out, vals_in, vbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return OS_ERR_CUDA;
+    return OS_OK;
+  }
+
+  // zero: status word, done counter, tile counters, histograms
+  if (cudaMemsetAsync(w, 0, plan.layout.bin_offset_offset, s) != cudaSuccess) return OS_ERR_CUDA;
+  rc = run_histogram(plan, key_type, keys_in, n, begin_bit, end_bit, w, true, s);
+  if (rc != OS_OK) return rc;
+
+  uint32_t* header = reinterpret_cast<uint32_t*>(w);
+  const uint32_t* offsets = reinterpret_cast<const uint32_t*>(w + plan.layout.bin_offset_offset);
+  void* alt_keys = w + plan.layout.alt_keys_offset;
+  uint32_t* alt_vals = reinterpret_cast<uint32_t*>(w + plan.layout.alt_values_offset);
+  const bool aligned_in = reinterpret_cast<uintptr_t>(keys_in) % 16 == 0 &&
+                          (!pairs || reinterpret_cast<uintptr_t>(vals_in) % 16 == 0);
+  const bool aligned_out = reinterpret_cast<uintptr_t>(keys_out) % 16 == 0 &&
+                           (!pairs || reinterpret_cast<uintptr_t>(vals_out) % 16 == 0);
+
+  const void* src_k = keys_in;
+  const uint32_t* src_v = vals_in;
+  bool src_aligned = aligned_in;
+  for (int pass = 0; pass < plan.places; ++pass) {
+    // ping-pong so that the last pass writes keys_out
+    const bool to_out = ((plan.places - 1 - pass) % 2) == 0;
+    void* dst_k = to_out ? keys_out : alt_keys;
+    uint32_t* dst_v = to_out ? vals_out : alt_vals;
+    PassArgs a{};
+    a.keys_in = src_k;
+    a.keys_out = dst_k;
+    a.vals_in = pairs ? src_v : nullptr;
+    a.vals_out = pairs ? dst_v : nullptr;
+    a.n = (uint32_t)n;
+    a.num_tiles = plan.tiles;
+    a.shift = begin_bit + kRadixBits * pass;
+    const int width = end_bit - a.shift < kRadixBits ? end_bit - a.shift : kRadixBits;
+    a.mask = (1u << width) - 1u;
+    a.flip_in = is_float(key_type) && pass == 0;
+    a.flip_out = is_float(key_type) && pass == plan.places - 1;
+    a.use_bulk = src_aligned ? 1 : 0;
+    a.bin_offsets = offsets + pass * kRadix;
+    a.status = reinterpret_cast<uint32_t*>(w + plan.layout.status_offset[pass & 1]);
+    a.status_clear = pass + 1 < plan.places
+                         ? reinterpret_cast<uint32_t*>(w + plan.layout.status_offset[(pass + 1) & 1])
+                         : nullptr;
+    a.tile_counter = header + kTileCounterWord + pass % 8;
+    a.error = header;
+    a.spin_limit = g_spin_limit;
+    a.fault_tile = g_fault_tile;
+    if (pass >= 8) {
+      // more than 8 passes cannot happen with 8-bit digits of <= 64-bit keys
+      return OS_ERR_INVALID_ARG;
+    }
+    if (launch_binning(plan.key_bits, pairs, a, s) != cudaSuccess) return OS_ERR_CUDA;
+    src_k = dst_k;
+    src_v = dst_v;
+    src_aligned = to_out ? aligned_out : true;
+  }
+  return OS_OK;
+}
+
+}  // namespace
+}  // namespace onesweep
+
+using namespace onesweep;
+
+extern "C" {
+
+size_t os_sort_workspace_bytes(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_bit) {
+  Plan plan;
+  if (make_plan(key_type, n, value_bytes, begin_bit, end_bit, &plan) != OS_OK) return 0;
+  return plan.layout.total_bytes;
+}
+
+int os_sort_workspace_layout(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_bit,
+                             os_workspace_layout* layout) {
+  if (!layout) return OS_ERR_INVALID_ARG;
+  Plan plan;
+  int rc = make_plan(key_type, n, value_bytes, begin_bit, end_bit, &plan);
+  if (rc != OS_OK) return rc;
+  *layout = plan.layout;
+  return OS_OK;
+}
+
+int os_sort_keys(int key_type, const void* keys_in, void* keys_out, uint64_t n, int begin_bit, int end_bit,
+                 void* ws, size_t ws_bytes, void* stream) {
+  return run_sort(key_type, keys_in, keys_out, nullptr, nullptr, n, begin_bit, end_bit, ws, ws_bytes, stream);
+}
+
+int os_sort_pairs(int key_type, const void* keys_in, void* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
+                  uint64_t n, int begin_bit, int end_bit, void* ws, size_t ws_bytes, void* stream) {
+  if (!vals_in || !vals_out) return OS_ERR_INVALID_ARG;
+  return run_sort(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws, ws_bytes, stream);
+}
+
+int os_digit_histograms(int key_type, const void* keys_in, uint64_t n, int begin_bit, int end_bit,
+                        uint32_t* hist_out, uint32_t* offsets_out, void* ws, size_t ws_bytes, void* stream) {
+  Plan plan;
+  int rc = make_plan(key_type, n, 0, begin_bit, end_bit, &plan);
+  if (rc != OS_OK) return rc;
+  if (!ws || ws_bytes < plan.layout.total_bytes) return OS_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(ws) % 16) return OS_ERR_INVALID_ARG;
+  if (n > 0 && !keys_in) return OS_ERR_INVALID_ARG;
+  if (n > 0 && reinterpret_cast<uintptr_t>(keys_in) % (plan.key_bits / 8)) return OS_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  const size_t bytes = (size_t)plan.places * kRadix * 4;
+  if (plan.places == 0) return OS_OK;
+  // bin offsets are zeroed too, so n == 0 yields all-zero offsets
+  if (cudaMemsetAsync(w, 0, plan.layout.bin_offset_offset + bytes, s) != cudaSuccess) return OS_ERR_CUDA;
+  if (n > 0) {
+    rc = run_histogram(plan, key_type, keys_in, n, begin_bit, end_bit, w, false, s);
+    if (rc != OS_OK) return rc;
+  }
+  if (hist_out && cudaMemcpyAsync(hist_out, w + plan.layout.histogram_offset, bytes, cudaMemcpyDeviceToDevice, s) !=
+                      cudaSuccess)
+    return OS_ERR_CUDA;
+  if (offsets_out && cudaMemcpyAsync(offsets_out, w + plan.layout.bin_offset_offset, bytes,
+                                     cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return OS_ERR_CUDA;
+  return OS_OK;
+}
+
+int os_workspace_status(const void* ws, void* stream) {
+  if (!ws) return OS_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return OS_ERR_CUDA;
+  uint32_t word = 0;
+  if (cudaMemcpy(&word, ws, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return OS_ERR_CUDA;
+  if (word & kErrTimeout) return OS_ERR_TIMEOUT;
+  return OS_OK;
+}
+
+const char* os_status_string(int status) {
+  switch (status) {
+    case OS_OK: return "ok";
+    case OS_ERR_INVALID_ARG: return "invalid argument";
+    case OS_ERR_TOO_LARGE: return "too many keys (n must be below 2^30)";
+    case OS_ERR_WORKSPACE: return "workspace missing or too small";
+    case OS_ERR_CUDA: return "CUDA error";
+    case OS_ERR_TIMEOUT: return "chained-scan look-back wait ran past its limit";
+    default: return "unknown status";
+  }
+}
+
+void os_debug_set_lookback_fault(int64_t tile, uint32_t spin_limit) {
+  g_fault_tile = tile < 0 ? -1 : tile;
+  g_spin_limit = spin_limit == 0 ? kDefaultSpinLimit : spin_limit;
+}
+
+}  // extern "C"

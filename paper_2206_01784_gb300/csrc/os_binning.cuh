@@ -1,0 +1,276 @@
+// Phase 3 of Onesweep (arXiv 2206.01784, Section 3, "Chained scan
+// digit-binning kernel"; Figures 6-8): one single-pass digit-binning
+// iteration, ~2n global words moved per pass.
+//
+// One block per tile of T = NT * IPT keys. Per tile:
+//  1. tile id from a global atomic counter, so tiles run in order whatever the
+//     hardware's block schedule (the look-back then always makes progress);
+//  2. the tile's keys (and values) are staged into shared memory by bulk
+//     copies on the TMA engine (one elected thread, an mbarrier completes);
+//     the ragged last tile uses plain loads;
+//  3. homogeneous-tile short-circuit: if every key of the tile has the same
+//     digit, ranking and local reorganisation are skipped and the tile is
+//     written straight to its bin (Section 3, last paragraph of the kernel
+//     description);
+//  4. warp-level multi-split ranking: each warp walks its keys in 32-wide
+//     batches; __match_any_sync groups lanes by digit, the lowest lane of each
+//     group bumps the warp's per-digit counter in shared memory and shares the
+//     old value (Section 3, WLMS paragraph);
+//  5. block-wide scan of the per-warp counts: tile digit counts for the chained
+//     scan and tile-relative bin starts for the local reorganisation;
+//  6. thread i publishes (L, count of digit i) in the tile's status counter,
+//     the keys are reorganised into their local bins in shared memory, then
+//     thread i walks the preceding tiles' counters for digit i (decoupled
+//     look-back, bounded wait) and publishes (G, inclusive prefix);
+//  7. runs of keys (and values) are copied from the shared-memory bins to
+//     their global bins, consecutive threads writing consecutive addresses.
+#pragma once
+
+#include "os_common.cuh"
+#include "os_internal.h"
+
+namespace onesweep {
+
+template <int KBITS, bool PAIRS>
+struct BinningConfig {
+  static constexpr int NT = 512;                        // threads per block
+  static constexpr int IPT = KBITS == 32 ? 16 : 8;      // keys per thread
+  static constexpr int MIN_BLOCKS = 2;                  // resident blocks per SM
+  static constexpr int T = NT * IPT;                    // keys per tile
+  static constexpr int NW = NT / 32;
+  using K = typename KeyWord<KBITS>::type;
+  static constexpr size_t kbuf_bytes = (size_t)T * sizeof(K);
+  static constexpr size_t vbuf_bytes = PAIRS ? (size_t)T * 4 : 0;
+  static constexpr size_t whist_bytes = (size_t)NW * kRadix * 4;
+  static constexpr size_t small_bytes = 2 * kRadix * 4 + 64 * 4 + 2 * 8;
+  static constexpr size_t smem_bytes = kbuf_bytes + vbuf_bytes + whist_bytes + small_bytes;
+};
+
+template <int KBITS, bool PAIRS>
+__global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS>::NT, BinningConfig<KBITS, PAIRS>::MIN_BLOCKS)
+    binning_kernel(PassArgs a) {
+  using C = BinningConfig<KBITS, PAIRS>;
+  using K = typename C::K;
+  constexpr int NT = C::NT, IPT = C::IPT, T = C::T, NW = C::NW;
+  constexpr uint32_t FULL = 0xFFFFFFFFu;
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  K* kbuf = reinterpret_cast<K*>(smem);
+  uint32_t* vbuf = reinterpret_cast<uint32_t*>(smem + C::kbuf_bytes);
+  uint32_t* whist = reinterpret_cast<uint32_t*>(smem + C::kbuf_bytes + C::vbuf_bytes);  // [NW][256]
+  uint32_t* dstart = whist + NW * kRadix;   // [256] tile-local start of each digit's bin
+  uint32_t* gbase = dstart + kRadix;        // [256] global index of local position 0 of each bin
+  uint32_t* misc = gbase + kRadix;          // [64] scan scratch, tile id
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(misc + 64);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  // 1. tile id
+  if (tid == 0) {
+    misc[NW + 1] = atomicAdd(a.tile_counter, 1u);
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    fence_mbar_init();
+  }
+  for (int i = tid; i < NW * kRadix; i += NT) whist[i] = 0;
+  __syncthreads();
+  const uint32_t tile = misc[NW + 1];
+  if (tile >= a.num_tiles) return;  // only if the workspace's counters were not reset
+  const uint32_t start = tile * (uint32_t)T;
+  const uint32_t count = min((uint32_t)T, a.n - start);
+  const bool bulk = a.use_bulk && count == (uint32_t)T;
+
+  // 2. stage the tile
+  const K* keys_in = static_cast<const K*>(a.keys_in) + start;
+  if (bulk) {
+    if (tid == 0) {
+      mbar_arrive_expect_tx(&mbar[0], (uint32_t)C::kbuf_bytes);
+      bulk_copy_g2s(kbuf, keys_in, (uint32_t)C::kbuf_bytes, &mbar[0]);
+      if (PAIRS) {
+        mbar_arrive_expect_tx(&mbar[1], (uint32_t)C::vbuf_bytes);
+        bulk_copy_g2s(vbuf, a.vals_in + start, (uint32_t)C::vbuf_bytes, &mbar[1]);
+      }
+    }
+  } else {
+    for (uint32_t i = tid; i < count; i += NT) kbuf[i] = keys_in[i];
+    if (PAIRS)
+      for (uint32_t i = tid; i < count; i += NT) vbuf[i] = a.vals_in[start + i];
+  }
+
+  // the next pass's status counters of this tile start at N
+  if (a.status_clear && tid < kRadix) a.status_clear[(size_t)tile * kRadix + tid] = 0u;
+  const uint32_t bin_offset = tid < kRadix ? a.bin_offsets[tid] : 0u;
+  uint32_t* status = a.status + (size_t)tile * kRadix;
+  const bool publish = (int64_t)tile != a.fault_tile;
+
+  if (bulk) {
+    if (!mbar_wait_bounded(&mbar[0], 0, kBulkWaitLimit)) atomicOr(a.error, kErrTimeout);
+  } else {
+    __syncthreads();
+  }
+
+  // keys of this thread: warp-striped, batch i of warp w covers tile positions
+  // [w*IPT*32 + i*32, +32), so batch order and lane order are input order
+  K key[IPT];
+  const uint32_t wbase = (uint32_t)warp * IPT * 32;
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    const uint32_t idx = wbase + i * 32 + lane;
+    K k = idx < count ? kbuf[idx] : K(0);
+    key[i] = a.flip_in ? flip_to_ordered(k) : k;
+  }
+
+  // 3. homogeneous-tile check
+  const K first = a.flip_in ? flip_to_ordered(kbuf[0]) : kbuf[0];
+  const uint32_t d0 = digit_of(first, a.shift, a.mask);
+  bool same = true;
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    const uint32_t idx = wbase + i * 32 + lane;
+    if (idx < count && digit_of(key[i], a.shift, a.mask) != d0) same = false;
+  }
+  const bool homogeneous = __syncthreads_and(same) != 0;
+
+  uint32_t digit_count = 0;  // thread d < 256: keys of digit d in this tile
+  uint32_t rank[IPT];
+  uint32_t val[PAIRS ? IPT : 1];
+
+  if (homogeneous) {
+    if (PAIRS && bulk && !mbar_wait_bounded(&mbar[1], 0, kBulkWaitLimit)) atomicOr(a.error, kErrTimeout);
+    if (tid < kRadix) {
+      digit_count = (uint32_t)tid == d0 ? count : 0u;
+      dstart[tid] = 0u;
+      if (publish)
+        st_relaxed_gpu(status + tid, ((tile == 0 ? kFlagGlobal : kFlagLocal) << kStatusShift) | digit_count);
+    }
+  } else {
+    // 4. warp-level multi-split ranking
+    uint32_t* wh = whist + warp * kRadix;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      const uint32_t idx = wbase + i * 32 + lane;
+      const bool valid = idx < count;
+      const uint32_t d = digit_of(key[i], a.shift, a.mask);
+      const uint32_t peers = __match_any_sync(FULL, valid ? d : 0xFFFFFFFFu);
+      const int leader = __ffs(peers) - 1;
+      uint32_t old = 0;
+      if (valid && lane == leader) {
+        old = wh[d];
+        wh[d] = old + __popc(peers);
+      }
+      old = __shfl_sync(FULL, old, leader);
+      rank[i] = old + __popc(peers & lanemask_lt());
+      __syncwarp();
+    }
+    if (PAIRS) {
+      if (bulk && !mbar_wait_bounded(&mbar[1], 0, kBulkWaitLimit)) atomicOr(a.error, kErrTimeout);
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        const uint32_t idx = wbase + i * 32 + lane;
+        val[i] = idx < count ? vbuf[idx] : 0u;
+      }
+    }
+    __syncthreads();
+
+    // 5. tile digit counts, publish L, per-warp exclusive offsets
+    if (tid < kRadix) {
+#pragma unroll
+      for (int w = 0; w < NW; ++w) digit_count += whist[w * kRadix + tid];
+      if (publish)
+        st_relaxed_gpu(status + tid, ((tile == 0 ? kFlagGlobal : kFlagLocal) << kStatusShift) | digit_count);
+    }
+    const uint32_t excl = block_exclusive_sum<NT>(tid < kRadix ? digit_count : 0u, misc);
+    if (tid < kRadix) {
+      uint32_t run = excl;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t c = whist[w * kRadix + tid];
+        whist[w * kRadix + tid] = run;
+        run += c;
+      }
+      dstart[tid] = excl;
+    }
+    __syncthreads();
+
+    // 6a. local reorganisation into shared-memory bins
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      const uint32_t idx = wbase + i * 32 + lane;
+      if (idx < count) {
+        const uint32_t pos = wh[digit_of(key[i], a.shift, a.mask)] + rank[i];
+        kbuf[pos] = key[i];
+        if (PAIRS) vbuf[pos] = val[i];
+      }
+    }
+  }
+
+  // 6b. decoupled look-back for digit tid over the preceding tiles
+  if (tid < kRadix) {
+    uint32_t exclusive = 0;
+    if (tile > 0) {
+      int64_t k = (int64_t)tile - 1;
+      uint32_t spins = 0;
+      while (k >= 0) {
+        const uint32_t s = ld_relaxed_gpu(a.status + (size_t)k * kRadix + tid);
+        const uint32_t flag = s >> kStatusShift;
+        if (flag == kFlagNotReady) {
+          if (++spins >= a.spin_limit) {
+            atomicOr(a.error, kErrTimeout);
+            break;
+          }
+          if ((spins & 255u) == 0 && (ld_relaxed_gpu(a.error) & kErrTimeout)) break;
+          continue;
+        }
+        exclusive += s & kValueMask;
+        if (flag == kFlagGlobal) break;
+        --k;
+      }
+      if (publish) st_relaxed_gpu(status + tid, (kFlagGlobal << kStatusShift) | (exclusive + digit_count));
+    }
+    gbase[tid] = bin_offset + exclusive - dstart[tid];
+  }
+  __syncthreads();
+
+  // 7. coalesced scatter of each local bin run to its global bin
+  K* keys_out = static_cast<K*>(a.keys_out);
+  if (homogeneous) {
+    const uint32_t g0 = gbase[d0];
+    for (uint32_t j = tid; j < count; j += NT) {
+      K k = kbuf[j];
+      if (a.flip_in) k = flip_to_ordered(k);
+      if (a.flip_out) k = flip_from_ordered(k);
+      const uint32_t g = g0 + j;
+      if (g < a.n) {
+        keys_out[g] = k;
+        if (PAIRS) a.vals_out[g] = vbuf[j];
+      }
+    }
+  } else {
+    for (uint32_t j = tid; j < count; j += NT) {
+      const K k = kbuf[j];
+      const uint32_t g = gbase[digit_of(k, a.shift, a.mask)] + j;
+      if (g < a.n) {
+        keys_out[g] = a.flip_out ? flip_from_ordered(k) : k;
+        if (PAIRS) a.vals_out[g] = vbuf[j];
+      }
+    }
+  }
+}
+
+template <int KBITS, bool PAIRS>
+cudaError_t launch_binning_t(const PassArgs& a, cudaStream_t s) {
+  using C = BinningConfig<KBITS, PAIRS>;
+  static int configured_device = -1;  // one attribute call per device switch
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_device != dev) {
+    cudaError_t e = cudaFuncSetAttribute(binning_kernel<KBITS, PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::smem_bytes);
+    if (e != cudaSuccess) return e;
+    configured_device = dev;
+  }
+  binning_kernel<KBITS, PAIRS><<<a.num_tiles, C::NT, C::smem_bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace onesweep

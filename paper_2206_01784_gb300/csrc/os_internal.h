@@ -1,0 +1,54 @@
+// Host-side interface between the C ABI (os_api.cu) and the kernel
+// translation units. Plain structs of device pointers and sizes.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace onesweep {
+
+// Phase 1 + 2 (Section 3, "Upfront histogram kernel", "Exclusive sum kernel").
+struct HistArgs {
+  const void* keys;          // n keys (device)
+  uint64_t n;
+  int flip;                  // float keys: apply the sign-flip before taking digits
+  int num_places;            // p
+  int begin_bit;             // place i covers bits [begin_bit + 8i, min(+8, end_bit))
+  int end_bit;
+  uint32_t* hist;            // [p][256] zeroed by the caller (device)
+  uint32_t* offsets;         // [p][256] written by the last block (device)
+  uint32_t* done_counter;    // zeroed by the caller (device)
+  uint32_t* clear;           // words to zero on the way (status slab of pass 0), may be null
+  uint64_t clear_words;
+};
+
+// Phase 3, one digit-binning pass (Section 3, "Chained scan digit-binning kernel").
+struct PassArgs {
+  const void* keys_in;
+  void* keys_out;
+  const uint32_t* vals_in;   // null for keys only
+  uint32_t* vals_out;
+  uint32_t n;
+  uint32_t num_tiles;
+  int shift;                 // digit = (ordered key >> shift) & mask
+  uint32_t mask;
+  int flip_in;               // apply the float sign-flip to loaded keys
+  int flip_out;              // undo it on stored keys
+  int use_bulk;              // inputs 16-byte aligned: stage full tiles with bulk copies
+  const uint32_t* bin_offsets;  // [256] global bin offsets of this place
+  uint32_t* status;          // [num_tiles][256] status counters, zeroed
+  uint32_t* status_clear;    // [num_tiles][256] slab of the next pass, to zero (may be null)
+  uint32_t* tile_counter;    // zeroed; hands out tile ids in launch order
+  uint32_t* error;           // device status word
+  uint32_t spin_limit;       // look-back polls before giving up
+  int64_t fault_tile;        // test hook: tile that never publishes (-1 = none)
+};
+
+// Tile geometry of the binning kernel for a key width / payload combination.
+uint32_t binning_tile_keys(int key_bits, bool pairs);
+
+cudaError_t launch_histogram(int key_bits, const HistArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_binning(int key_bits, bool pairs, const PassArgs& a, cudaStream_t s);
+
+}  // namespace onesweep

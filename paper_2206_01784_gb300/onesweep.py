@@ -1,0 +1,212 @@
+"""Thin Python binding of the C ABI in ``include/onesweep.h`` (libonesweep.so).
+
+The functions named ``os_*`` mirror the C entry points one to one and take
+raw device pointers (ints), sizes and a ``cudaStream_t`` (int, 0 = legacy
+default stream). The torch helpers below them only marshal tensors: they
+allocate outputs and the workspace with torch and pass ``data_ptr()`` and the
+current stream. Every step of the sort runs in the library's CUDA kernels;
+there is no CPU fallback - if the library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libonesweep.so")
+
+OS_KEY_U32, OS_KEY_U64, OS_KEY_F32, OS_KEY_F64 = 0, 1, 2, 3
+KEY_TYPES = {"u32": OS_KEY_U32, "u64": OS_KEY_U64, "f32": OS_KEY_F32, "f64": OS_KEY_F64}
+KEY_BITS = {OS_KEY_U32: 32, OS_KEY_U64: 64, OS_KEY_F32: 32, OS_KEY_F64: 64}
+
+OS_OK, OS_ERR_INVALID_ARG, OS_ERR_TOO_LARGE, OS_ERR_WORKSPACE, OS_ERR_CUDA, OS_ERR_TIMEOUT = range(6)
+
+
+class OnesweepError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {os_status_string(status)} (status {status})")
+        self.status = status
+
+
+class WorkspaceLayout(ctypes.Structure):
+    _fields_ = [
+        ("total_bytes", ctypes.c_size_t),
+        ("status_offset", ctypes.c_size_t * 2),
+        ("histogram_offset", ctypes.c_size_t),
+        ("bin_offset_offset", ctypes.c_size_t),
+        ("alt_keys_offset", ctypes.c_size_t),
+        ("alt_values_offset", ctypes.c_size_t),
+        ("tile_keys", ctypes.c_uint32),
+        ("num_tiles", ctypes.c_uint32),
+        ("num_places", ctypes.c_uint32),
+    ]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libonesweep.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2206_01784_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    i32, u32, u64, i64, sz, vp = (ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
+                                  ctypes.c_size_t, ctypes.c_void_p)
+    lib.os_sort_workspace_bytes.restype = sz
+    lib.os_sort_workspace_bytes.argtypes = [i32, u64, i32, i32, i32]
+    lib.os_sort_workspace_layout.restype = i32
+    lib.os_sort_workspace_layout.argtypes = [i32, u64, i32, i32, i32, ctypes.POINTER(WorkspaceLayout)]
+    lib.os_sort_keys.restype = i32
+    lib.os_sort_keys.argtypes = [i32, vp, vp, u64, i32, i32, vp, sz, vp]
+    lib.os_sort_pairs.restype = i32
+    lib.os_sort_pairs.argtypes = [i32, vp, vp, vp, vp, u64, i32, i32, vp, sz, vp]
+    lib.os_digit_histograms.restype = i32
+    lib.os_digit_histograms.argtypes = [i32, vp, u64, i32, i32, vp, vp, vp, sz, vp]
+    lib.os_workspace_status.restype = i32
+    lib.os_workspace_status.argtypes = [vp, vp]
+    lib.os_status_string.restype = ctypes.c_char_p
+    lib.os_status_string.argtypes = [i32]
+    lib.os_debug_set_lookback_fault.restype = None
+    lib.os_debug_set_lookback_fault.argtypes = [i64, u32]
+    _lib = lib
+    return lib
+
+
+# ---------------------------------------------------------------- C ABI mirror
+
+def os_sort_workspace_bytes(key_type: int, n: int, value_bytes: int, begin_bit: int, end_bit: int) -> int:
+    return int(load().os_sort_workspace_bytes(key_type, n, value_bytes, begin_bit, end_bit))
+
+
+def os_sort_workspace_layout(key_type: int, n: int, value_bytes: int, begin_bit: int, end_bit: int) -> WorkspaceLayout:
+    lay = WorkspaceLayout()
+    rc = load().os_sort_workspace_layout(key_type, n, value_bytes, begin_bit, end_bit, ctypes.byref(lay))
+    if rc != OS_OK:
+        raise OnesweepError(rc, "os_sort_workspace_layout")
+    return lay
+
+
+def os_sort_keys(key_type, keys_in, keys_out, n, begin_bit, end_bit, ws, ws_bytes, stream) -> int:
+    return int(load().os_sort_keys(key_type, keys_in, keys_out, n, begin_bit, end_bit, ws, ws_bytes, stream))
+
+
+def os_sort_pairs(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws, ws_bytes,
+                  stream) -> int:
+    return int(load().os_sort_pairs(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws,
+                                    ws_bytes, stream))
+
+
+def os_digit_histograms(key_type, keys_in, n, begin_bit, end_bit, hist_out, offsets_out, ws, ws_bytes,
+                        stream) -> int:
+    return int(load().os_digit_histograms(key_type, keys_in, n, begin_bit, end_bit, hist_out, offsets_out, ws,
+                                          ws_bytes, stream))
+
+
+def os_workspace_status(ws, stream) -> int:
+    return int(load().os_workspace_status(ws, stream))
+
+
+def os_status_string(status: int) -> str:
+    try:
+        return load().os_status_string(status).decode()
+    except RuntimeError:
+        return f"status {status}"
+
+
+def os_debug_set_lookback_fault(tile: int, spin_limit: int = 0) -> None:
+    load().os_debug_set_lookback_fault(tile, spin_limit)
+
+
+# ---------------------------------------------------------------- torch helpers
+
+def _torch():
+    import torch
+    return torch
+
+
+def key_type_of(t, key_type: str | int | None = None) -> int:
+    """Key type for a tensor: explicit, or float32/float64 by dtype, else unsigned by width."""
+    torch = _torch()
+    if key_type is not None:
+        return KEY_TYPES[key_type] if isinstance(key_type, str) else int(key_type)
+    if t.dtype == torch.float32:
+        return OS_KEY_F32
+    if t.dtype == torch.float64:
+        return OS_KEY_F64
+    if t.element_size() == 4:
+        return OS_KEY_U32
+    if t.element_size() == 8:
+        return OS_KEY_U64
+    raise TypeError(f"unsupported key dtype {t.dtype}")
+
+
+def _stream_ptr(stream) -> int:
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+def workspace(key_type: int, n: int, value_bytes: int, begin_bit: int, end_bit: int, device):
+    torch = _torch()
+    nbytes = os_sort_workspace_bytes(key_type, n, value_bytes, begin_bit, end_bit)
+    if nbytes == 0:
+        raise OnesweepError(OS_ERR_INVALID_ARG, "os_sort_workspace_bytes")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def _check(rc: int, where: str):
+    if rc != OS_OK:
+        raise OnesweepError(rc, where)
+
+
+def sort_keys(keys, begin_bit: int = 0, end_bit: int | None = None, key_type=None, out=None, ws=None,
+              stream=None):
+    """Stable ascending sort of a 1-D CUDA tensor of keys; returns the sorted keys."""
+    torch = _torch()
+    kt = key_type_of(keys, key_type)
+    end_bit = KEY_BITS[kt] if end_bit is None else end_bit
+    keys = keys.contiguous()
+    n = keys.numel()
+    out = torch.empty_like(keys) if out is None else out
+    ws = workspace(kt, n, 0, begin_bit, end_bit, keys.device) if ws is None else ws
+    _check(os_sort_keys(kt, keys.data_ptr(), out.data_ptr(), n, begin_bit, end_bit, ws.data_ptr(), ws.numel(),
+                        _stream_ptr(stream)), "os_sort_keys")
+    return out
+
+
+def sort_pairs(keys, values, begin_bit: int = 0, end_bit: int | None = None, key_type=None, keys_out=None,
+               values_out=None, ws=None, stream=None):
+    """Stable ascending sort of (key, uint32 value) pairs; returns (keys, values)."""
+    torch = _torch()
+    kt = key_type_of(keys, key_type)
+    end_bit = KEY_BITS[kt] if end_bit is None else end_bit
+    keys = keys.contiguous()
+    values = values.contiguous()
+    if values.element_size() != 4 or values.numel() != keys.numel():
+        raise ValueError("values must be a 4-byte tensor with one value per key")
+    n = keys.numel()
+    keys_out = torch.empty_like(keys) if keys_out is None else keys_out
+    values_out = torch.empty_like(values) if values_out is None else values_out
+    ws = workspace(kt, n, 4, begin_bit, end_bit, keys.device) if ws is None else ws
+    _check(os_sort_pairs(kt, keys.data_ptr(), keys_out.data_ptr(), values.data_ptr(), values_out.data_ptr(), n,
+                         begin_bit, end_bit, ws.data_ptr(), ws.numel(), _stream_ptr(stream)), "os_sort_pairs")
+    return keys_out, values_out
+
+
+def digit_histograms(keys, begin_bit: int = 0, end_bit: int | None = None, key_type=None, stream=None):
+    """Digit counts and global bin offsets of every place: two int32 tensors [p, 256]."""
+    torch = _torch()
+    kt = key_type_of(keys, key_type)
+    end_bit = KEY_BITS[kt] if end_bit is None else end_bit
+    keys = keys.contiguous()
+    n = keys.numel()
+    p = (end_bit - begin_bit + 7) // 8
+    hist = torch.empty((p, 256), dtype=torch.int32, device=keys.device)
+    offs = torch.empty((p, 256), dtype=torch.int32, device=keys.device)
+    ws = workspace(kt, n, 0, begin_bit, end_bit, keys.device)
+    _check(os_digit_histograms(kt, keys.data_ptr(), n, begin_bit, end_bit, hist.data_ptr(), offs.data_ptr(),
+                               ws.data_ptr(), ws.numel(), _stream_ptr(stream)), "os_digit_histograms")
+    return hist, offs

@@ -30,3 +30,15 @@ def read_golden(name):
                 parts = line.split()
                 out.setdefault("rows", []).append([float(x) for x in parts])
     return out
+
+
+def pytest_sessionstart(session):
+    """Build the oracle, the workload generator and the CUDA library in-tree
+    (each is a no-op when up to date; nvcc cross-compiles without a GPU)."""
+    import oracle
+    from paper_2206_01784_gb300 import build as cuda_build
+    from paper_2206_01784_gb300 import workload
+
+    oracle.build()
+    workload.build()
+    cuda_build.build()

@@ -1,0 +1,98 @@
+"""The C-ABI library loads, exports every declared entry point and validates
+arguments on the host (no GPU: nothing here reaches a CUDA call)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2206_01784_gb300 import onesweep as osw
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names.update(re.findall(r"^OS_API\s+[\w\s\*]+?\b(os_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for n in ("os_sort_keys", "os_sort_pairs", "os_sort_workspace_bytes", "os_workspace_status"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = osw.load()
+    out = subprocess.run(["nm", "-D", "--defined-only", osw.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT\s+(os_\w+)", out))
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in exported, name
+
+
+def test_library_built_for_sm103a():
+    out = subprocess.run(["cuobjdump", "--list-elf", osw.LIB_PATH], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_workspace_sizes():
+    u32 = osw.OS_KEY_U32
+    assert osw.os_sort_workspace_bytes(u32, 1 << 20, 0, 0, 32) > (1 << 20) * 4
+    assert osw.os_sort_workspace_bytes(u32, 1 << 20, 4, 0, 32) > osw.os_sort_workspace_bytes(u32, 1 << 20, 0, 0, 32)
+    assert osw.os_sort_workspace_bytes(7, 100, 0, 0, 32) == 0       # bad key type
+    assert osw.os_sort_workspace_bytes(u32, 100, 2, 0, 32) == 0     # bad value width
+    assert osw.os_sort_workspace_bytes(u32, 100, 0, 0, 33) == 0     # bad bit range
+    assert osw.os_sort_workspace_bytes(u32, 1 << 30, 0, 0, 32) == 0  # too large
+    assert osw.os_sort_workspace_bytes(osw.OS_KEY_U64, 100, 0, 0, 64) > 0
+
+
+def test_workspace_layout():
+    lay = osw.os_sort_workspace_layout(osw.OS_KEY_U32, 10_000_000, 4, 0, 32)
+    assert lay.num_places == 4
+    assert lay.num_tiles == (10_000_000 + lay.tile_keys - 1) // lay.tile_keys
+    offs = [lay.histogram_offset, lay.bin_offset_offset, lay.status_offset[0], lay.status_offset[1],
+            lay.alt_keys_offset, lay.alt_values_offset]
+    assert offs == sorted(offs) and all(o % 256 == 0 for o in offs)
+    assert lay.status_offset[1] - lay.status_offset[0] >= lay.num_tiles * 256 * 4
+    assert lay.alt_values_offset - lay.alt_keys_offset >= 10_000_000 * 4
+    assert lay.total_bytes >= lay.alt_values_offset + 10_000_000 * 4
+    one = osw.os_sort_workspace_layout(osw.OS_KEY_U32, 1000, 0, 0, 8)
+    assert one.num_places == 1
+    narrow = osw.os_sort_workspace_layout(osw.OS_KEY_U64, 1000, 0, 5, 50)
+    assert narrow.num_places == 6
+
+
+def test_host_validation_without_gpu():
+    u32 = osw.OS_KEY_U32
+    fake = 1 << 40  # never dereferenced: every call below fails validation first
+    ws_bytes = osw.os_sort_workspace_bytes(u32, 1000, 0, 0, 32)
+    assert osw.os_sort_keys(u32, fake, fake + 8192, 1 << 30, 0, 32, fake + 65536, 1 << 40, 0) == osw.OS_ERR_TOO_LARGE
+    assert osw.os_sort_keys(u32, fake, fake + 8192, 1000, 0, 40, fake + 65536, ws_bytes, 0) == osw.OS_ERR_INVALID_ARG
+    assert osw.os_sort_keys(u32, fake, fake + 8192, 1000, 9, 8, fake + 65536, ws_bytes, 0) == osw.OS_ERR_INVALID_ARG
+    assert osw.os_sort_keys(9, fake, fake + 8192, 1000, 0, 32, fake + 65536, ws_bytes, 0) == osw.OS_ERR_INVALID_ARG
+    assert osw.os_sort_keys(u32, fake, fake + 8192, 1000, 0, 32, fake + 65536, ws_bytes - 1, 0) == osw.OS_ERR_WORKSPACE
+    assert osw.os_sort_keys(u32, fake, fake + 8192, 1000, 0, 32, None, ws_bytes, 0) == osw.OS_ERR_WORKSPACE
+    # overlapping input and output
+    assert osw.os_sort_keys(u32, fake, fake + 400, 1000, 0, 32, fake + 65536, ws_bytes, 0) == osw.OS_ERR_INVALID_ARG
+    # misaligned keys
+    assert osw.os_sort_keys(u32, fake + 2, fake + 8192, 1000, 0, 32, fake + 65536, ws_bytes, 0) == osw.OS_ERR_INVALID_ARG
+    # pairs need both value pointers
+    assert osw.os_sort_pairs(u32, fake, fake + 8192, None, fake + 20000, 1000, 0, 32, fake + 65536, 1 << 30,
+                             0) == osw.OS_ERR_INVALID_ARG
+    # n == 0 is a no-op
+    assert osw.os_sort_keys(u32, None, None, 0, 0, 32, None, 0, 0) == osw.OS_OK
+
+
+def test_status_strings():
+    for s in range(6):
+        assert osw.os_status_string(s)
+    assert "2^30" in osw.os_status_string(osw.OS_ERR_TOO_LARGE)
