@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 Onesweep sort (arXiv 2206.01784) on 256M uint32
+keys with uint32 index values, the paper's Section 4 workload shape (seeded,
+synthetic, uniform random keys).
+
+One step = one full sort through the C ABI (os_sort_pairs): the header memset,
+the all-places histogram + exclusive sum, and 4 chained-scan binning passes.
+Inputs (2 GiB of keys + values) are resident in HBM and far larger than L2, so
+no L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torchrun) every rank sorts its own array of the same
+size: independent replicas, weak scaling, no collective on the data path.
+``--impl reference`` times the CPU oracle instead (rank 0 only).
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GKeys/s @256M u32 keys, % HBM roofline; batched vs per-array GKeys/s, p99 ms"
+UNIT = "GKeys/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--log2n", type=int, default=28, help="keys per GPU = 2^log2n")
+    p.add_argument("--dist", default="uniform")
+    p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=10)
+    return p.parse_args()
+
+
+def workload_name(n, dist, seed):
+    size = f"{n >> 20}M" if n >= (1 << 20) else str(n)
+    return f"{size} u32 keys + u32 index values, {dist} keys (seed {seed})"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2206_01784_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_tag: str, n: int):
+    """DRAM bytes per launch from a committed ncu summary whose source hash
+    matches the current kernels (None when absent or stale)."""
+    want = source_hash()
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md")) + glob.glob(os.path.join(ROOT, "profiles", "*.txt"))):
+        fields = {}
+        for line in open(f):
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                fields[k.strip()] = v.strip().strip("`")
+        if fields.get("kernel_tag") == kernel_tag and fields.get("source_hash") == want:
+            try:
+                per_key = float(fields["dram_bytes_per_key"])
+            except (KeyError, ValueError):
+                continue
+            return per_key * n
+    return None
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", self.gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_smi_id(torch, dev_index: int) -> str:
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev_index).uuid)
+        if uuid:
+            return uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        return vis.split(",")[dev_index]
+    return str(dev_index)
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def time_oracle(n: int, dist: str, seed: int, repeats: int = 1):
+    """The CPU oracle as it stands (single thread), on n pairs of the workload."""
+    import oracle
+    from paper_2206_01784_gb300 import workload
+
+    keys = workload.keys("u32", dist, n, seed)
+    vals = workload.iota_u32(n)
+    times = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        oracle.sort("u32", keys, vals)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle timed on the host cores, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    # bounded sample per step (a slice of the 2^28 workload): about a minute
+    # of CPU work in total at the oracle's ~14 Mkeys/s, at most 2^22 per step
+    n = 1 << 22
+    while n > (1 << 16) and n * (args.steps + args.warmup) > 840_000_000:
+        n >>= 1
+    times = time_oracle(n, args.dist, args.seed, repeats=args.warmup + args.steps)[args.warmup:]
+    total = sum(times)
+    value = n * len(times) / total / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / len(times) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic", "impl": "reference",
+        "config": {"workload": workload_name(1 << args.log2n, args.dist, args.seed),
+                   "sample_keys_per_step": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n} u32 pairs of the same distribution per step, single-threaded C oracle",
+                         "cpu": cpu_model()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2206_01784_gb300 import onesweep as osw
+    from paper_2206_01784_gb300 import workload
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    osw.load()
+    n = 1 << args.log2n
+    seed = args.seed + 1000 * rank
+    keys_np = workload.keys("u32", args.dist, n, seed)
+    vals_np = workload.iota_u32(n)
+    keys = torch.from_numpy(keys_np.view(np.int32)).to(dev)
+    vals = torch.from_numpy(vals_np.view(np.int32)).to(dev)
+    keys_out = torch.empty_like(keys)
+    vals_out = torch.empty_like(vals)
+    kt = osw.OS_KEY_U32
+    lay = osw.os_sort_workspace_layout(kt, n, 4, 0, 32)
+    ws = torch.empty(lay.total_bytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    def step():
+        rc = osw.os_sort_pairs(kt, keys.data_ptr(), keys_out.data_ptr(), vals.data_ptr(), vals_out.data_ptr(), n, 0,
+                               32, ws.data_ptr(), ws.numel(), sp)
+        if rc != osw.OS_OK:
+            raise osw.OnesweepError(rc, "os_sort_pairs")
+
+    warmup = max(args.warmup, 3)
+    for _ in range(warmup):
+        step()
+    barrier()
+
+    sampler = ClockSampler(gpu_smi_id(torch, local))
+    sampler.start()
+    time.sleep(0.3)
+    capacity = args.steps * (lay.num_places + 1) + 16
+    osw.os_profile_start(capacity)
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step()
+    t_end.record(stream)
+    barrier()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    prof_rc, launches, recs = osw.os_profile_stop(capacity)
+    clocks = sampler.stop()
+    status = osw.os_workspace_status(ws.data_ptr(), sp)
+    if status != osw.OS_OK:
+        raise osw.OnesweepError(status, "device status after timed steps")
+
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    ms_per_step = max_ms / args.steps
+    value = world * n * args.steps / (max_ms / 1e3) / 1e9
+
+    # sanity: output sorted and values a permutation carrying their keys (outside the timed region)
+    ko64 = keys_out.to(torch.int64) & 0xFFFFFFFF
+    ok = bool((ko64[1:] >= ko64[:-1]).all().item())
+    del ko64
+    gathered = keys[vals_out.to(torch.int64)]
+    ok = ok and bool(torch.equal(gathered, keys_out))
+    del gathered
+    if not ok:
+        raise RuntimeError("sorted output failed the sanity check")
+
+    # roofline of the dominant kernel (the binning pass)
+    peak, peak_kind = hbm_peak()
+    bin_ms = [ms for k, _, ms in recs if k == 1]
+    hist_ms = [ms for k, _, ms in recs if k == 0]
+    bin_avg = statistics.mean(bin_ms)
+    bytes_per_pass = n * 2 * (4 + 4)
+    achieved = bytes_per_pass / (bin_avg / 1e3) / 1e9
+    traffic = profiled_traffic("binning_u32_pairs", n)
+    step_bytes = n * 4 + lay.num_places * bytes_per_pass
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "binning_kernel<32, pairs>", "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": bytes_per_pass, "avg_launch_ms": bin_avg}
+    step_roofline = {"achieved": step_bytes / (ms_per_step / 1e3) / 1e9, "peak": peak,
+                     "frac": step_bytes / (ms_per_step / 1e3) / 1e9 / peak, "algorithmic_bytes_per_step": step_bytes,
+                     "histogram_avg_ms": statistics.mean(hist_ms) if hist_ms else None,
+                     "binning_avg_ms": bin_avg}
+
+    # end to end: pinned host buffers, H2D of the inputs and D2H of the result in the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        hk = torch.from_numpy(keys_np.view(np.int32)).pin_memory()
+        hv = torch.from_numpy(vals_np.view(np.int32)).pin_memory()
+        hko = torch.empty_like(hk).pin_memory()
+        hvo = torch.empty_like(hv).pin_memory()
+
+        def e2e_step():
+            keys.copy_(hk, non_blocking=True)
+            vals.copy_(hv, non_blocking=True)
+            step()
+            hko.copy_(keys_out, non_blocking=True)
+            hvo.copy_(vals_out, non_blocking=True)
+
+        e2e_step()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        et = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(et, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * n * args.e2e_steps / (float(et.item()) / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": hk.numel() * 4 + hv.numel() * 4,
+               "d2h_bytes_per_step": hko.numel() * 4 + hvo.numel() * 4, "steps": args.e2e_steps}
+        ok = np.array_equal(hko.numpy().view(np.uint32)[:: 1 << 16], keys_out.cpu().numpy().view(np.uint32)[:: 1 << 16])
+        if not ok:
+            raise RuntimeError("end-to-end result differs from the device result")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = n // 2
+        times = time_oracle(sample, args.dist, seed)
+        cpu = {"value": sample / times[0] / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{sample} u32 pairs (half the workload, same distribution), single-threaded C oracle, "
+                         f"{times[0]:.1f} s", "cpu": cpu_model(), "nproc": os.cpu_count()}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": workload_name(n, args.dist, args.seed), "keys_per_gpu": n, "key_type": "u32",
+                       "values": "u32 (input index)", "bits": [0, 32], "places": lay.num_places,
+                       "tile_keys": lay.tile_keys, "parallelism": f"replicas x{world}",
+                       "l2": "no flush: 2 GiB of inputs per step, larger than L2"},
+            "roofline": roofline, "roofline_step": step_roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks, "gpu": torch.cuda.get_device_name(dev),
+            "paper_context": "A100-80GB: 29.4 GKey/s, 256M u32 keys only (different hardware and workload)",
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

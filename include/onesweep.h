@@ -147,6 +147,23 @@ OS_API const char *os_status_string(int status);
  */
 OS_API void os_debug_set_lookback_fault(int64_t tile, uint32_t spin_limit);
 
+/*
+ * Launch timing for benchmarks (not part of the method). os_profile_start
+ * makes every later kernel launch of the library record a CUDA event pair on
+ * its own stream, for up to `capacity` launches. os_profile_stop waits for
+ * those events, writes up to `max` records to `out` (host array), stores how
+ * many launches were recorded in *count, releases the events and switches
+ * recording off. Process-wide, not thread-safe. Both return an os_status.
+ */
+typedef struct {
+    int kernel;   /* 0 = histogram (phases 1-2), 1 = digit binning (phase 3) */
+    int pass;     /* digit place of a binning launch, -1 for the histogram */
+    float ms;     /* device time between the pair of events */
+} os_launch_time;
+
+OS_API int os_profile_start(int capacity);
+OS_API int os_profile_stop(os_launch_time *out, int max, int *count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,6 +44,32 @@ constexpr size_t kTileCounterWord = 16;
 int64_t g_fault_tile = -1;
 uint32_t g_spin_limit = kDefaultSpinLimit;
 
+// Launch timing (os_profile_start / os_profile_stop).
+struct ProfiledLaunch {
+  cudaEvent_t start, stop;
+  int kernel, pass;
+};
+ProfiledLaunch* g_prof = nullptr;
+int g_prof_capacity = 0;
+int g_prof_used = 0;
+int g_prof_seen = 0;
+
+// Records the start event of a launch if profiling is on; returns its slot.
+int prof_begin(int kernel, int pass, cudaStream_t s) {
+  if (!g_prof) return -1;
+  ++g_prof_seen;
+  if (g_prof_used >= g_prof_capacity) return -1;
+  ProfiledLaunch& p = g_prof[g_prof_used];
+  p.kernel = kernel;
+  p.pass = pass;
+  if (cudaEventRecord(p.start, s) != cudaSuccess) return -1;
+  return g_prof_used++;
+}
+
+void prof_end(int slot, cudaStream_t s) {
+  if (slot >= 0) cudaEventRecord(g_prof[slot].stop, s);
+}
+
 size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 int key_bits_of(int key_type) {
@@ -138,7 +164,10 @@ int run_histogram(const Plan& plan, int key_type, const void* keys, uint64_t n, 
   h.clear_words = clear_slab0 ? (uint64_t)plan.tiles * kRadix : 0;
   const int sms = device_sm_count();
   if (sms <= 0) return OS_ERR_CUDA;
-  return launch_histogram(plan.key_bits, h, sms, s) == cudaSuccess ? OS_OK : OS_ERR_CUDA;
+  const int slot = prof_begin(0, -1, s);
+  const cudaError_t e = launch_histogram(plan.key_bits, h, sms, s);
+  prof_end(slot, s);
+  return e == cudaSuccess ? OS_OK : OS_ERR_CUDA;
 }
 
 int run_sort(int key_type, const void* keys_in, void* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
@@ -231,7 +260,10 @@ int run_sort(int key_type, const void* keys_in, void* keys_out, const uint32_t* 
       // more than 8 passes cannot happen with 8-bit digits of <= 64-bit keys
       return OS_ERR_INVALID_ARG;
     }
-    if (launch_binning(plan.key_bits, pairs, a, s) != cudaSuccess) return OS_ERR_CUDA;
+    const int slot = prof_begin(1, pass, s);
+    const cudaError_t e = launch_binning(plan.key_bits, pairs, a, s);
+    prof_end(slot, s);
+    if (e != cudaSuccess) return OS_ERR_CUDA;
     src_k = dst_k;
     src_v = dst_v;
     src_aligned = to_out ? aligned_out : true;
@@ -321,6 +353,47 @@ const char* os_status_string(int status) {
     case OS_ERR_TIMEOUT: return "chained-scan look-back wait ran past its limit";
     default: return "unknown status";
   }
+}
+
+int os_profile_start(int capacity) {
+  if (g_prof || capacity <= 0) return OS_ERR_INVALID_ARG;
+  ProfiledLaunch* p = new ProfiledLaunch[capacity];
+  for (int i = 0; i < capacity; ++i) {
+    if (cudaEventCreate(&p[i].start) != cudaSuccess || cudaEventCreate(&p[i].stop) != cudaSuccess) {
+      for (int j = 0; j <= i; ++j) {
+        cudaEventDestroy(p[j].start);
+        cudaEventDestroy(p[j].stop);
+      }
+      delete[] p;
+      return OS_ERR_CUDA;
+    }
+  }
+  g_prof = p;
+  g_prof_capacity = capacity;
+  g_prof_used = 0;
+  g_prof_seen = 0;
+  return OS_OK;
+}
+
+int os_profile_stop(os_launch_time* out, int max, int* count) {
+  if (!g_prof) return OS_ERR_INVALID_ARG;
+  int rc = OS_OK;
+  for (int i = 0; i < g_prof_used; ++i) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(g_prof[i].stop) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, g_prof[i].start, g_prof[i].stop) != cudaSuccess)
+      rc = OS_ERR_CUDA;
+    if (out && i < max) out[i] = os_launch_time{g_prof[i].kernel, g_prof[i].pass, ms};
+  }
+  if (count) *count = g_prof_seen;
+  for (int i = 0; i < g_prof_capacity; ++i) {
+    cudaEventDestroy(g_prof[i].start);
+    cudaEventDestroy(g_prof[i].stop);
+  }
+  delete[] g_prof;
+  g_prof = nullptr;
+  g_prof_capacity = g_prof_used = g_prof_seen = 0;
+  return rc;
 }
 
 void os_debug_set_lookback_fault(int64_t tile, uint32_t spin_limit) {

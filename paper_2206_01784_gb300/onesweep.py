@@ -42,6 +42,10 @@ class WorkspaceLayout(ctypes.Structure):
     ]
 
 
+class LaunchTime(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("pass_", ctypes.c_int), ("ms", ctypes.c_float)]
+
+
 _lib = None
 
 
@@ -71,6 +75,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.os_status_string.argtypes = [i32]
     lib.os_debug_set_lookback_fault.restype = None
     lib.os_debug_set_lookback_fault.argtypes = [i64, u32]
+    lib.os_profile_start.restype = i32
+    lib.os_profile_start.argtypes = [i32]
+    lib.os_profile_stop.restype = i32
+    lib.os_profile_stop.argtypes = [ctypes.POINTER(LaunchTime), i32, ctypes.POINTER(i32)]
     _lib = lib
     return lib
 
@@ -118,6 +126,19 @@ def os_status_string(status: int) -> str:
 
 def os_debug_set_lookback_fault(tile: int, spin_limit: int = 0) -> None:
     load().os_debug_set_lookback_fault(tile, spin_limit)
+
+
+def os_profile_start(capacity: int) -> int:
+    return int(load().os_profile_start(capacity))
+
+
+def os_profile_stop(max_records: int = 1 << 16):
+    """Returns (status, recorded launch count, [(kernel, pass, ms), ...])."""
+    buf = (LaunchTime * max_records)()
+    cnt = ctypes.c_int(0)
+    rc = int(load().os_profile_stop(buf, max_records, ctypes.byref(cnt)))
+    recs = [(buf[i].kernel, buf[i].pass_, float(buf[i].ms)) for i in range(min(cnt.value, max_records))]
+    return rc, cnt.value, recs
 
 
 # ---------------------------------------------------------------- torch helpers

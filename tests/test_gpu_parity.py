@@ -224,6 +224,7 @@ def test_inputs_preserved_and_repeatable():
 
 
 def test_stream_argument():
+    _dev()
     n = 200_000
     keys = make_keys("u32", "uniform", n, seed=43)
     s = torch.cuda.Stream()
