@@ -46,12 +46,14 @@ def parse_args():
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--keys-only", action="store_true", help="sort keys without values")
     return p.parse_args()
 
 
-def workload_name(n, dist, seed):
+def workload_name(n, dist, seed, pairs=True):
     size = f"{n >> 20}M" if n >= (1 << 20) else str(n)
-    return f"{size} u32 keys + u32 index values, {dist} keys (seed {seed})"
+    payload = " + u32 index values" if pairs else " only"
+    return f"{size} u32 keys{payload}, {dist} keys (seed {seed})"
 
 
 def source_hash() -> str:
@@ -238,14 +240,18 @@ def main():
     keys_out = torch.empty_like(keys)
     vals_out = torch.empty_like(vals)
     kt = osw.OS_KEY_U32
-    lay = osw.os_sort_workspace_layout(kt, n, 4, 0, 32)
+    pairs = not args.keys_only
+    lay = osw.os_sort_workspace_layout(kt, n, 4 if pairs else 0, 0, 32)
     ws = torch.empty(lay.total_bytes, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
 
     def step():
-        rc = osw.os_sort_pairs(kt, keys.data_ptr(), keys_out.data_ptr(), vals.data_ptr(), vals_out.data_ptr(), n, 0,
-                               32, ws.data_ptr(), ws.numel(), sp)
+        if pairs:
+            rc = osw.os_sort_pairs(kt, keys.data_ptr(), keys_out.data_ptr(), vals.data_ptr(), vals_out.data_ptr(), n,
+                                   0, 32, ws.data_ptr(), ws.numel(), sp)
+        else:
+            rc = osw.os_sort_keys(kt, keys.data_ptr(), keys_out.data_ptr(), n, 0, 32, ws.data_ptr(), ws.numel(), sp)
         if rc != osw.OS_OK:
             raise osw.OnesweepError(rc, "os_sort_pairs")
 
@@ -285,9 +291,10 @@ def main():
     ko64 = keys_out.to(torch.int64) & 0xFFFFFFFF
     ok = bool((ko64[1:] >= ko64[:-1]).all().item())
     del ko64
-    gathered = keys[vals_out.to(torch.int64)]
-    ok = ok and bool(torch.equal(gathered, keys_out))
-    del gathered
+    if pairs:
+        gathered = keys[vals_out.to(torch.int64)]
+        ok = ok and bool(torch.equal(gathered, keys_out))
+        del gathered
     if not ok:
         raise RuntimeError("sorted output failed the sanity check")
 
@@ -296,12 +303,12 @@ def main():
     bin_ms = [ms for k, _, ms in recs if k == 1]
     hist_ms = [ms for k, _, ms in recs if k == 0]
     bin_avg = statistics.mean(bin_ms)
-    bytes_per_pass = n * 2 * (4 + 4)
+    bytes_per_pass = n * 2 * (4 + (4 if pairs else 0))
     achieved = bytes_per_pass / (bin_avg / 1e3) / 1e9
-    traffic = profiled_traffic("binning_u32_pairs", n)
+    traffic = profiled_traffic("binning_u32_pairs" if pairs else "binning_u32_keys", n)
     step_bytes = n * 4 + lay.num_places * bytes_per_pass
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "binning_kernel<32, pairs>", "peak_kind": peak_kind,
+                "traffic": traffic, "kernel": "binning_kernel<32, pairs>" if pairs else "binning_kernel<32, keys>", "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_per_pass, "avg_launch_ms": bin_avg}
     step_roofline = {"achieved": step_bytes / (ms_per_step / 1e3) / 1e9, "peak": peak,
                      "frac": step_bytes / (ms_per_step / 1e3) / 1e9 / peak, "algorithmic_bytes_per_step": step_bytes,
@@ -318,10 +325,12 @@ def main():
 
         def e2e_step():
             keys.copy_(hk, non_blocking=True)
-            vals.copy_(hv, non_blocking=True)
+            if pairs:
+                vals.copy_(hv, non_blocking=True)
             step()
             hko.copy_(keys_out, non_blocking=True)
-            hvo.copy_(vals_out, non_blocking=True)
+            if pairs:
+                hvo.copy_(vals_out, non_blocking=True)
 
         e2e_step()
         barrier()
@@ -336,8 +345,8 @@ def main():
         if world > 1:
             dist.all_reduce(et, op=dist.ReduceOp.MAX)
         e2e = {"value": world * n * args.e2e_steps / (float(et.item()) / 1e3) / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": hk.numel() * 4 + hv.numel() * 4,
-               "d2h_bytes_per_step": hko.numel() * 4 + hvo.numel() * 4, "steps": args.e2e_steps}
+               "h2d_bytes_per_step": hk.numel() * 4 + (hv.numel() * 4 if pairs else 0),
+               "d2h_bytes_per_step": hko.numel() * 4 + (hvo.numel() * 4 if pairs else 0), "steps": args.e2e_steps}
         ok = np.array_equal(hko.numpy().view(np.uint32)[:: 1 << 16], keys_out.cpu().numpy().view(np.uint32)[:: 1 << 16])
         if not ok:
             raise RuntimeError("end-to-end result differs from the device result")
@@ -355,8 +364,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": workload_name(n, args.dist, args.seed), "keys_per_gpu": n, "key_type": "u32",
-                       "values": "u32 (input index)", "bits": [0, 32], "places": lay.num_places,
+            "config": {"workload": workload_name(n, args.dist, args.seed, pairs), "keys_per_gpu": n,
+                       "key_type": "u32", "values": "u32 (input index)" if pairs else None, "bits": [0, 32], "places": lay.num_places,
                        "tile_keys": lay.tile_keys, "parallelism": f"replicas x{world}",
                        "l2": "no flush: 2 GiB of inputs per step, larger than L2"},
             "roofline": roofline, "roofline_step": step_roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -8,6 +8,7 @@
 // launches on the caller's stream. Nothing is allocated and nothing waits on
 // the host.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "../../include/onesweep.h"
@@ -16,8 +17,8 @@
 
 namespace onesweep {
 
-cudaError_t launch_binning32(bool pairs, const PassArgs& a, cudaStream_t s);
-cudaError_t launch_binning64(bool pairs, const PassArgs& a, cudaStream_t s);
+cudaError_t launch_binning32(bool pairs, bool match, const PassArgs& a, cudaStream_t s);
+cudaError_t launch_binning64(bool pairs, bool match, const PassArgs& a, cudaStream_t s);
 uint32_t binning_tile_keys32(bool pairs);
 uint32_t binning_tile_keys64(bool pairs);
 
@@ -25,8 +26,21 @@ uint32_t binning_tile_keys(int key_bits, bool pairs) {
   return key_bits == 32 ? binning_tile_keys32(pairs) : binning_tile_keys64(pairs);
 }
 
+// Digit-ranking variant of the binning kernel: one __match_any_sync per key
+// (default) or the paper's one-ballot-per-digit-bit WLMS. ONESWEEP_RANK=ballot
+// or =match overrides the default (read once per process).
+bool rank_with_match() {
+  static int choice = -1;
+  if (choice < 0) {
+    const char* e = std::getenv("ONESWEEP_RANK");
+    choice = (e && std::strcmp(e, "ballot") == 0) ? 0 : 1;
+  }
+  return choice == 1;
+}
+
 cudaError_t launch_binning(int key_bits, bool pairs, const PassArgs& a, cudaStream_t s) {
-  return key_bits == 32 ? launch_binning32(pairs, a, s) : launch_binning64(pairs, a, s);
+  const bool match = rank_with_match();
+  return key_bits == 32 ? launch_binning32(pairs, match, a, s) : launch_binning64(pairs, match, a, s);
 }
 
 namespace {

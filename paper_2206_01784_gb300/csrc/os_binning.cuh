@@ -7,23 +7,29 @@
 //     hardware's block schedule (the look-back then always makes progress);
 //  2. the tile's keys (and values) are staged into shared memory by bulk
 //     copies on the TMA engine (one elected thread, an mbarrier completes);
-//     the ragged last tile uses plain loads;
+//     the ragged last tile and unaligned inputs use plain loads;
 //  3. homogeneous-tile short-circuit: if every key of the tile has the same
 //     digit, ranking and local reorganisation are skipped and the tile is
 //     written straight to its bin (Section 3, last paragraph of the kernel
 //     description);
 //  4. warp-level multi-split ranking: each warp walks its keys in 32-wide
-//     batches; __match_any_sync groups lanes by digit, the lowest lane of each
-//     group bumps the warp's per-digit counter in shared memory and shares the
-//     old value (Section 3, WLMS paragraph);
+//     batches; lanes holding the same digit are found either with one
+//     __match_any_sync or, as in the paper, with one ballot per digit bit
+//     ANDed together; the lowest lane of each group bumps the warp's
+//     per-digit counter in shared memory and the group reads the old value
+//     (Section 3, WLMS paragraph);
 //  5. block-wide scan of the per-warp counts: tile digit counts for the chained
 //     scan and tile-relative bin starts for the local reorganisation;
 //  6. thread i publishes (L, count of digit i) in the tile's status counter,
-//     the keys are reorganised into their local bins in shared memory, then
-//     thread i walks the preceding tiles' counters for digit i (decoupled
-//     look-back, bounded wait) and publishes (G, inclusive prefix);
+//     the keys (then the values) are reorganised into their local bins in
+//     shared memory, then thread i walks the preceding tiles' counters for
+//     digit i (decoupled look-back, bounded wait) and publishes
+//     (G, inclusive prefix);
 //  7. runs of keys (and values) are copied from the shared-memory bins to
 //     their global bins, consecutive threads writing consecutive addresses.
+//
+// Full tiles take a branch-light path with no per-key bounds checks; only the
+// ragged last tile of a pass checks every index.
 #pragma once
 
 #include "os_common.cuh"
@@ -46,60 +52,47 @@ struct BinningConfig {
   static constexpr size_t smem_bytes = kbuf_bytes + vbuf_bytes + whist_bytes + small_bytes;
 };
 
-template <int KBITS, bool PAIRS>
-__global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS>::NT, BinningConfig<KBITS, PAIRS>::MIN_BLOCKS)
-    binning_kernel(PassArgs a) {
+// Lanes of the warp whose digit equals this lane's (valid lanes only).
+template <bool MATCH>
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid, uint32_t valid_mask) {
+  if (MATCH) {
+    return __match_any_sync(0xFFFFFFFFu, valid ? d : 0xFFFFFFFFu);
+  } else {
+    // one vote per digit bit (Section 3, WLMS): keep the lanes that agree on it
+    uint32_t peers = valid_mask;
+#pragma unroll
+    for (int b = 0; b < kRadixBits; ++b) {
+      const uint32_t v = __ballot_sync(0xFFFFFFFFu, (d >> b) & 1u);
+      const uint32_t m = 0u - ((d >> b) & 1u);  // all ones where this lane's bit is set
+      peers &= ~(v ^ m);
+    }
+    return valid ? peers : 0u;
+  }
+}
+
+template <int KBITS, bool PAIRS, bool MATCH, bool FULL>
+__device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* smem, uint32_t tile, uint32_t count,
+                                             bool bulk) {
   using C = BinningConfig<KBITS, PAIRS>;
   using K = typename C::K;
-  constexpr int NT = C::NT, IPT = C::IPT, T = C::T, NW = C::NW;
-  constexpr uint32_t FULL = 0xFFFFFFFFu;
+  constexpr int NT = C::NT, IPT = C::IPT, NW = C::NW;
 
-  extern __shared__ __align__(128) unsigned char smem[];
   K* kbuf = reinterpret_cast<K*>(smem);
   uint32_t* vbuf = reinterpret_cast<uint32_t*>(smem + C::kbuf_bytes);
   uint32_t* whist = reinterpret_cast<uint32_t*>(smem + C::kbuf_bytes + C::vbuf_bytes);  // [NW][256]
   uint32_t* dstart = whist + NW * kRadix;   // [256] tile-local start of each digit's bin
   uint32_t* gbase = dstart + kRadix;        // [256] global index of local position 0 of each bin
-  uint32_t* misc = gbase + kRadix;          // [64] scan scratch, tile id
+  uint32_t* misc = gbase + kRadix;          // [64] scan scratch
   uint64_t* mbar = reinterpret_cast<uint64_t*>(misc + 64);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-  // 1. tile id
-  if (tid == 0) {
-    misc[NW + 1] = atomicAdd(a.tile_counter, 1u);
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
-    fence_mbar_init();
-  }
-  for (int i = tid; i < NW * kRadix; i += NT) whist[i] = 0;
-  __syncthreads();
-  const uint32_t tile = misc[NW + 1];
-  if (tile >= a.num_tiles) return;  // only if the workspace's counters were not reset
-  const uint32_t start = tile * (uint32_t)T;
-  const uint32_t count = min((uint32_t)T, a.n - start);
-  const bool bulk = a.use_bulk && count == (uint32_t)T;
-
-  // 2. stage the tile
-  const K* keys_in = static_cast<const K*>(a.keys_in) + start;
-  if (bulk) {
-    if (tid == 0) {
-      mbar_arrive_expect_tx(&mbar[0], (uint32_t)C::kbuf_bytes);
-      bulk_copy_g2s(kbuf, keys_in, (uint32_t)C::kbuf_bytes, &mbar[0]);
-      if (PAIRS) {
-        mbar_arrive_expect_tx(&mbar[1], (uint32_t)C::vbuf_bytes);
-        bulk_copy_g2s(vbuf, a.vals_in + start, (uint32_t)C::vbuf_bytes, &mbar[1]);
-      }
-    }
-  } else {
-    for (uint32_t i = tid; i < count; i += NT) kbuf[i] = keys_in[i];
-    if (PAIRS)
-      for (uint32_t i = tid; i < count; i += NT) vbuf[i] = a.vals_in[start + i];
-  }
+  const int shift = a.shift;
+  const uint32_t mask = a.mask;
+  const bool flip_in = a.flip_in != 0;
 
   // the next pass's status counters of this tile start at N
   if (a.status_clear && tid < kRadix) a.status_clear[(size_t)tile * kRadix + tid] = 0u;
-  const uint32_t bin_offset = tid < kRadix ? a.bin_offsets[tid] : 0u;
+  const uint32_t bin_offset = tid < kRadix ? __ldg(a.bin_offsets + tid) : 0u;
   uint32_t* status = a.status + (size_t)tile * kRadix;
   const bool publish = (int64_t)tile != a.fault_tile;
 
@@ -112,28 +105,26 @@ __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS>::NT, BinningConfig
   // keys of this thread: warp-striped, batch i of warp w covers tile positions
   // [w*IPT*32 + i*32, +32), so batch order and lane order are input order
   K key[IPT];
-  const uint32_t wbase = (uint32_t)warp * IPT * 32;
+  const uint32_t wbase = (uint32_t)warp * IPT * 32 + lane;
 #pragma unroll
   for (int i = 0; i < IPT; ++i) {
-    const uint32_t idx = wbase + i * 32 + lane;
-    K k = idx < count ? kbuf[idx] : K(0);
-    key[i] = a.flip_in ? flip_to_ordered(k) : k;
+    const uint32_t idx = wbase + i * 32;
+    K k = (FULL || idx < count) ? kbuf[idx] : K(0);
+    key[i] = flip_in ? flip_to_ordered(k) : k;
   }
 
   // 3. homogeneous-tile check
-  const K first = a.flip_in ? flip_to_ordered(kbuf[0]) : kbuf[0];
-  const uint32_t d0 = digit_of(first, a.shift, a.mask);
+  const K first = flip_in ? flip_to_ordered(kbuf[0]) : kbuf[0];
+  const uint32_t d0 = digit_of(first, shift, mask);
   bool same = true;
 #pragma unroll
   for (int i = 0; i < IPT; ++i) {
-    const uint32_t idx = wbase + i * 32 + lane;
-    if (idx < count && digit_of(key[i], a.shift, a.mask) != d0) same = false;
+    const bool valid = FULL || wbase + i * 32 < count;
+    same &= !valid || digit_of(key[i], shift, mask) == d0;
   }
   const bool homogeneous = __syncthreads_and(same) != 0;
 
   uint32_t digit_count = 0;  // thread d < 256: keys of digit d in this tile
-  uint32_t rank[IPT];
-  uint32_t val[PAIRS ? IPT : 1];
 
   if (homogeneous) {
     if (PAIRS && bulk && !mbar_wait_bounded(&mbar[1], 0, kBulkWaitLimit)) atomicOr(a.error, kErrTimeout);
@@ -144,31 +135,26 @@ __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS>::NT, BinningConfig
         st_relaxed_gpu(status + tid, ((tile == 0 ? kFlagGlobal : kFlagLocal) << kStatusShift) | digit_count);
     }
   } else {
-    // 4. warp-level multi-split ranking
+    // 4. warp-level multi-split ranking; rank = keys of the same digit before
+    //    this one in the warp's part of the tile
     uint32_t* wh = whist + warp * kRadix;
+    uint32_t rank2[IPT / 2];  // two 16-bit ranks per register (ranks < T <= 2^16)
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
-      const uint32_t idx = wbase + i * 32 + lane;
-      const bool valid = idx < count;
-      const uint32_t d = digit_of(key[i], a.shift, a.mask);
-      const uint32_t peers = __match_any_sync(FULL, valid ? d : 0xFFFFFFFFu);
-      const int leader = __ffs(peers) - 1;
-      uint32_t old = 0;
-      if (valid && lane == leader) {
-        old = wh[d];
-        wh[d] = old + __popc(peers);
-      }
-      old = __shfl_sync(FULL, old, leader);
-      rank[i] = old + __popc(peers & lanemask_lt());
+      const bool valid = FULL || wbase + i * 32 < count;
+      const uint32_t valid_mask = FULL ? 0xFFFFFFFFu : __ballot_sync(0xFFFFFFFFu, valid);
+      const uint32_t d = digit_of(key[i], shift, mask);
+      const uint32_t peers = digit_peers<MATCH>(d, valid, valid_mask);
+      const uint32_t below = __popc(peers & lanemask_lt());
+      const uint32_t old = valid ? wh[d] : 0u;
       __syncwarp();
-    }
-    if (PAIRS) {
-      if (bulk && !mbar_wait_bounded(&mbar[1], 0, kBulkWaitLimit)) atomicOr(a.error, kErrTimeout);
-#pragma unroll
-      for (int i = 0; i < IPT; ++i) {
-        const uint32_t idx = wbase + i * 32 + lane;
-        val[i] = idx < count ? vbuf[idx] : 0u;
-      }
+      if (valid && below == 0) wh[d] = old + __popc(peers);
+      __syncwarp();
+      const uint32_t r = old + below;
+      if (i & 1)
+        rank2[i / 2] |= r << 16;
+      else
+        rank2[i / 2] = r;
     }
     __syncthreads();
 
@@ -192,15 +178,35 @@ __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS>::NT, BinningConfig
     }
     __syncthreads();
 
-    // 6a. local reorganisation into shared-memory bins
+    // 6a. local reorganisation of the keys into shared-memory bins; for pairs
+    //     the positions are kept (two 16-bit positions per register)
+    uint32_t pos2[PAIRS ? IPT / 2 : 1];
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
-      const uint32_t idx = wbase + i * 32 + lane;
-      if (idx < count) {
-        const uint32_t pos = wh[digit_of(key[i], a.shift, a.mask)] + rank[i];
-        kbuf[pos] = key[i];
-        if (PAIRS) vbuf[pos] = val[i];
+      const bool valid = FULL || wbase + i * 32 < count;
+      const uint32_t r = (i & 1) ? (rank2[i / 2] >> 16) : (rank2[i / 2] & 0xFFFFu);
+      const uint32_t p = valid ? wh[digit_of(key[i], shift, mask)] + r : 0u;
+      if (valid) kbuf[p] = key[i];
+      if (PAIRS) {
+        if (i & 1)
+          pos2[i / 2] |= p << 16;
+        else
+          pos2[i / 2] = p;
       }
+    }
+    if (PAIRS) {
+      // values: read this thread's values, wait for every read, then scatter
+      if (bulk && !mbar_wait_bounded(&mbar[1], 0, kBulkWaitLimit)) atomicOr(a.error, kErrTimeout);
+      uint32_t val[IPT];
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        const uint32_t idx = wbase + i * 32;
+        val[i] = (FULL || idx < count) ? vbuf[idx] : 0u;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < IPT; ++i)
+        if (FULL || wbase + i * 32 < count) vbuf[(i & 1) ? (pos2[i / 2] >> 16) : (pos2[i / 2] & 0xFFFFu)] = val[i];
     }
   }
 
@@ -233,43 +239,106 @@ __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS>::NT, BinningConfig
 
   // 7. coalesced scatter of each local bin run to its global bin
   K* keys_out = static_cast<K*>(a.keys_out);
+  const bool flip_out = a.flip_out != 0;
   if (homogeneous) {
     const uint32_t g0 = gbase[d0];
-    for (uint32_t j = tid; j < count; j += NT) {
-      K k = kbuf[j];
-      if (a.flip_in) k = flip_to_ordered(k);
-      if (a.flip_out) k = flip_from_ordered(k);
-      const uint32_t g = g0 + j;
-      if (g < a.n) {
-        keys_out[g] = k;
-        if (PAIRS) a.vals_out[g] = vbuf[j];
+#pragma unroll 4
+    for (int i = 0; i < IPT; ++i) {
+      const uint32_t j = i * NT + tid;
+      if (FULL || j < count) {
+        K k = kbuf[j];
+        if (flip_in) k = flip_to_ordered(k);
+        if (flip_out) k = flip_from_ordered(k);
+        const uint32_t g = g0 + j;
+        if (g < a.n) {
+          keys_out[g] = k;
+          if (PAIRS) a.vals_out[g] = vbuf[j];
+        }
       }
     }
   } else {
-    for (uint32_t j = tid; j < count; j += NT) {
-      const K k = kbuf[j];
-      const uint32_t g = gbase[digit_of(k, a.shift, a.mask)] + j;
-      if (g < a.n) {
-        keys_out[g] = a.flip_out ? flip_from_ordered(k) : k;
-        if (PAIRS) a.vals_out[g] = vbuf[j];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      const uint32_t j = i * NT + tid;
+      if (FULL || j < count) {
+        const K k = kbuf[j];
+        const uint32_t g = gbase[digit_of(k, shift, mask)] + j;
+        if (g < a.n) {
+          keys_out[g] = flip_out ? flip_from_ordered(k) : k;
+          if (PAIRS) a.vals_out[g] = vbuf[j];
+        }
       }
     }
   }
 }
 
-template <int KBITS, bool PAIRS>
-cudaError_t launch_binning_t(const PassArgs& a, cudaStream_t s) {
+template <int KBITS, bool PAIRS, bool MATCH>
+__global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS>::NT, BinningConfig<KBITS, PAIRS>::MIN_BLOCKS)
+    binning_kernel(PassArgs a) {
   using C = BinningConfig<KBITS, PAIRS>;
-  static int configured_device = -1;  // one attribute call per device switch
+  using K = typename C::K;
+  constexpr int NT = C::NT, T = C::T, NW = C::NW;
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  K* kbuf = reinterpret_cast<K*>(smem);
+  uint32_t* vbuf = reinterpret_cast<uint32_t*>(smem + C::kbuf_bytes);
+  uint32_t* whist = reinterpret_cast<uint32_t*>(smem + C::kbuf_bytes + C::vbuf_bytes);
+  uint32_t* misc = whist + NW * kRadix + 2 * kRadix;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(misc + 64);
+  const int tid = threadIdx.x;
+
+  // 1. tile id
+  if (tid == 0) {
+    misc[NW + 1] = atomicAdd(a.tile_counter, 1u);
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    fence_mbar_init();
+  }
+  for (int i = tid; i < NW * kRadix; i += NT) whist[i] = 0;
+  __syncthreads();
+  const uint32_t tile = misc[NW + 1];
+  if (tile >= a.num_tiles) return;  // only if the workspace's counters were not reset
+  const uint32_t start = tile * (uint32_t)T;
+  const uint32_t count = min((uint32_t)T, a.n - start);
+  const bool full = count == (uint32_t)T;
+  const bool bulk = a.use_bulk && full;
+
+  // 2. stage the tile
+  const K* keys_in = static_cast<const K*>(a.keys_in) + start;
+  if (bulk) {
+    if (tid == 0) {
+      mbar_arrive_expect_tx(&mbar[0], (uint32_t)C::kbuf_bytes);
+      bulk_copy_g2s(kbuf, keys_in, (uint32_t)C::kbuf_bytes, &mbar[0]);
+      if (PAIRS) {
+        mbar_arrive_expect_tx(&mbar[1], (uint32_t)C::vbuf_bytes);
+        bulk_copy_g2s(vbuf, a.vals_in + start, (uint32_t)C::vbuf_bytes, &mbar[1]);
+      }
+    }
+  } else {
+    for (uint32_t i = tid; i < count; i += NT) kbuf[i] = keys_in[i];
+    if (PAIRS)
+      for (uint32_t i = tid; i < count; i += NT) vbuf[i] = a.vals_in[start + i];
+  }
+
+  if (full)
+    binning_tile<KBITS, PAIRS, MATCH, true>(a, smem, tile, count, bulk);
+  else
+    binning_tile<KBITS, PAIRS, MATCH, false>(a, smem, tile, count, bulk);
+}
+
+template <int KBITS, bool PAIRS>
+cudaError_t launch_binning_t(const PassArgs& a, cudaStream_t s, bool match) {
+  using C = BinningConfig<KBITS, PAIRS>;
+  static int configured_device[2] = {-1, -1};  // one attribute call per device switch
   int dev = 0;
   cudaGetDevice(&dev);
-  if (configured_device != dev) {
-    cudaError_t e = cudaFuncSetAttribute(binning_kernel<KBITS, PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::smem_bytes);
+  auto kern = match ? binning_kernel<KBITS, PAIRS, true> : binning_kernel<KBITS, PAIRS, false>;
+  if (configured_device[match] != dev) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bytes);
     if (e != cudaSuccess) return e;
-    configured_device = dev;
+    configured_device[match] = dev;
   }
-  binning_kernel<KBITS, PAIRS><<<a.num_tiles, C::NT, C::smem_bytes, s>>>(a);
+  kern<<<a.num_tiles, C::NT, C::smem_bytes, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -3,8 +3,8 @@
 
 namespace onesweep {
 
-cudaError_t launch_binning32(bool pairs, const PassArgs& a, cudaStream_t s) {
-  return pairs ? launch_binning_t<32, true>(a, s) : launch_binning_t<32, false>(a, s);
+cudaError_t launch_binning32(bool pairs, bool match, const PassArgs& a, cudaStream_t s) {
+  return pairs ? launch_binning_t<32, true>(a, s, match) : launch_binning_t<32, false>(a, s, match);
 }
 
 uint32_t binning_tile_keys32(bool pairs) {
