@@ -138,6 +138,22 @@ OS_API int os_workspace_status(const void *ws, void *stream);
 OS_API const char *os_status_string(int status);
 
 /*
+ * Tile geometry of the digit-binning kernel (tuning, not part of the method).
+ * There are os_num_tile_configs() geometries per key width and payload
+ * (keys only: value_bytes 0, pairs: 4); os_tile_config_keys() gives the keys
+ * per tile of one (0 for invalid arguments). os_set_tile_config() selects the
+ * geometry later calls use (process-wide, applied at launch time); results
+ * are identical under every geometry. Workspaces are sized for the smallest
+ * tile, so a workspace sized once fits every geometry. os_set_tile_config
+ * returns OS_OK or OS_ERR_INVALID_ARG; os_get_tile_config returns the active
+ * geometry or -1.
+ */
+OS_API int os_num_tile_configs(void);
+OS_API int os_tile_config_keys(int key_bits, int value_bytes, int cfg);
+OS_API int os_set_tile_config(int key_bits, int value_bytes, int cfg);
+OS_API int os_get_tile_config(int key_bits, int value_bytes);
+
+/*
  * Fault injection for tests of the look-back wait limit (not part of the
  * method). With tile >= 0, every later binning pass skips all status-counter
  * publishes of that tile, so the tiles after it wait until `spin_limit`

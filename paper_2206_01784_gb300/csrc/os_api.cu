@@ -17,30 +17,62 @@
 
 namespace onesweep {
 
-cudaError_t launch_binning32(bool pairs, bool match, const PassArgs& a, cudaStream_t s);
-cudaError_t launch_binning64(bool pairs, bool match, const PassArgs& a, cudaStream_t s);
-uint32_t binning_tile_keys32(bool pairs);
-uint32_t binning_tile_keys64(bool pairs);
+#define OS_DECLARE_BINNING(KB, PR)                                                        \
+  cudaError_t launch_binning##KB##_##PR##_f0(int, int, const PassArgs&, cudaStream_t);   \
+  cudaError_t launch_binning##KB##_##PR##_f1(int, int, const PassArgs&, cudaStream_t);   \
+  cudaError_t launch_binning##KB##_##PR##_f2(int, int, const PassArgs&, cudaStream_t);   \
+  cudaError_t launch_binning##KB##_##PR##_f3(int, int, const PassArgs&, cudaStream_t);   \
+  uint32_t binning_tile_keys##KB##_##PR(int cfg);
+OS_DECLARE_BINNING(32, pairs)
+OS_DECLARE_BINNING(32, keys)
+OS_DECLARE_BINNING(64, pairs)
+OS_DECLARE_BINNING(64, keys)
+#undef OS_DECLARE_BINNING
 
-uint32_t binning_tile_keys(int key_bits, bool pairs) {
-  return key_bits == 32 ? binning_tile_keys32(pairs) : binning_tile_keys64(pairs);
+using BinningLaunch = cudaError_t (*)(int, int, const PassArgs&, cudaStream_t);
+
+// [64-bit][pairs][float transform mode]
+const BinningLaunch kBinningLaunch[2][2][4] = {
+    {{launch_binning32_keys_f0, launch_binning32_keys_f1, launch_binning32_keys_f2, launch_binning32_keys_f3},
+     {launch_binning32_pairs_f0, launch_binning32_pairs_f1, launch_binning32_pairs_f2, launch_binning32_pairs_f3}},
+    {{launch_binning64_keys_f0, launch_binning64_keys_f1, launch_binning64_keys_f2, launch_binning64_keys_f3},
+     {launch_binning64_pairs_f0, launch_binning64_pairs_f1, launch_binning64_pairs_f2, launch_binning64_pairs_f3}}};
+
+// Binning kernel variants: tile geometry (4) x digit-ranking method (2);
+// variant v uses geometry v % 4 and ranking v / 4 (0: one ballot per digit
+// bit, 1: shared-memory lane masks).
+constexpr int kGeometries = 4;
+constexpr int kTileConfigs = 2 * kGeometries;
+
+// Active variant per (key width, keys only / pairs); set by
+// os_set_tile_config (the autotuner's hook).
+int g_tile_cfg[2][2] = {{0, 0}, {0, 0}};
+
+uint32_t tile_keys_for(int key_bits, bool pairs, int cfg) {
+  const int geo = cfg % kGeometries;
+  if (key_bits == 32) return pairs ? binning_tile_keys32_pairs(geo) : binning_tile_keys32_keys(geo);
+  return pairs ? binning_tile_keys64_pairs(geo) : binning_tile_keys64_keys(geo);
 }
 
-// Digit-ranking variant of the binning kernel: one __match_any_sync per key
-// (default) or the paper's one-ballot-per-digit-bit WLMS. ONESWEEP_RANK=ballot
-// or =match overrides the default (read once per process).
-bool rank_with_match() {
-  static int choice = -1;
-  if (choice < 0) {
-    const char* e = std::getenv("ONESWEEP_RANK");
-    choice = (e && std::strcmp(e, "ballot") == 0) ? 0 : 1;
+uint32_t binning_tile_keys(int key_bits, bool pairs) {
+  return tile_keys_for(key_bits, pairs, g_tile_cfg[key_bits == 64][pairs]);
+}
+
+// Smallest tile over all geometries: workspaces are sized for it, so any
+// geometry fits a workspace sized once.
+uint32_t min_tile_keys(int key_bits, bool pairs) {
+  uint32_t t = tile_keys_for(key_bits, pairs, 0);
+  for (int c = 1; c < kGeometries; ++c) {
+    const uint32_t u = tile_keys_for(key_bits, pairs, c);
+    if (u < t) t = u;
   }
-  return choice == 1;
+  return t;
 }
 
 cudaError_t launch_binning(int key_bits, bool pairs, const PassArgs& a, cudaStream_t s) {
-  const bool match = rank_with_match();
-  return key_bits == 32 ? launch_binning32(pairs, match, a, s) : launch_binning64(pairs, match, a, s);
+  const int cfg = g_tile_cfg[key_bits == 64][pairs];
+  const int flip = (a.flip_in ? 1 : 0) | (a.flip_out ? 2 : 0);
+  return kBinningLaunch[key_bits == 64][pairs][flip](cfg % kGeometries, cfg / kGeometries, a, s);
 }
 
 namespace {
@@ -118,6 +150,8 @@ int make_plan(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_
   plan->places = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
   plan->tile = binning_tile_keys(kb, plan->pairs);
   plan->tiles = (uint32_t)((n + plan->tile - 1) / plan->tile);
+  const uint32_t min_tile = min_tile_keys(kb, plan->pairs);
+  const uint64_t max_tiles = (n + min_tile - 1) / min_tile;
   os_workspace_layout& L = plan->layout;
   std::memset(&L, 0, sizeof(L));
   size_t off = kHeaderBytes;
@@ -125,7 +159,7 @@ int make_plan(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_
   off = round_up(off + (size_t)8 * kRadix * 4);
   L.bin_offset_offset = off;
   off = round_up(off + (size_t)8 * kRadix * 4);
-  const size_t slab = (size_t)plan->tiles * kRadix * 4;
+  const size_t slab = (size_t)max_tiles * kRadix * 4;
   L.status_offset[0] = off;
   off = round_up(off + slab);
   L.status_offset[1] = off;
@@ -408,6 +442,28 @@ int os_profile_stop(os_launch_time* out, int max, int* count) {
   g_prof = nullptr;
   g_prof_capacity = g_prof_used = g_prof_seen = 0;
   return rc;
+}
+
+int os_num_tile_configs(void) { return kTileConfigs; }
+
+int os_tile_config_keys(int key_bits, int value_bytes, int cfg) {
+  if ((key_bits != 32 && key_bits != 64) || (value_bytes != 0 && value_bytes != 4) || cfg < 0 ||
+      cfg >= kTileConfigs)
+    return 0;
+  return (int)tile_keys_for(key_bits, value_bytes == 4, cfg);
+}
+
+int os_set_tile_config(int key_bits, int value_bytes, int cfg) {
+  if ((key_bits != 32 && key_bits != 64) || (value_bytes != 0 && value_bytes != 4) || cfg < 0 ||
+      cfg >= kTileConfigs)
+    return OS_ERR_INVALID_ARG;
+  g_tile_cfg[key_bits == 64][value_bytes == 4] = cfg;
+  return OS_OK;
+}
+
+int os_get_tile_config(int key_bits, int value_bytes) {
+  if ((key_bits != 32 && key_bits != 64) || (value_bytes != 0 && value_bytes != 4)) return -1;
+  return g_tile_cfg[key_bits == 64][value_bytes == 4];
 }
 
 void os_debug_set_lookback_fault(int64_t tile, uint32_t spin_limit) {

@@ -1,0 +1,11 @@
+// Instantiations of the digit-binning kernel: 32-bit keys, pairs, float
+// transform mode 1 (bit 0: sign-flip on load, bit 1: undo on store).
+#include "os_binning.cuh"
+
+namespace onesweep {
+
+cudaError_t launch_binning32_pairs_f1(int cfg, int rank, const PassArgs& a, cudaStream_t s) {
+  return launch_binning_flip<32, true, 1>(a, s, cfg, rank);
+}
+
+}  // namespace onesweep

@@ -13,11 +13,12 @@
 //     written straight to its bin (Section 3, last paragraph of the kernel
 //     description);
 //  4. warp-level multi-split ranking: each warp walks its keys in 32-wide
-//     batches; lanes holding the same digit are found either with one
-//     __match_any_sync or, as in the paper, with one ballot per digit bit
-//     ANDed together; the lowest lane of each group bumps the warp's
-//     per-digit counter in shared memory and the group reads the old value
-//     (Section 3, WLMS paragraph);
+//     batches; lanes holding the same digit are found, as in the paper, with
+//     one ballot per digit bit ANDed together (on GB300 this measured 1.7x
+//     faster than one __match_any_sync per key, which saturates the ADU
+//     pipe); the lowest lane of each group bumps the warp's per-digit counter
+//     in shared memory and the group reads the old value (Section 3, WLMS
+//     paragraph);
 //  5. block-wide scan of the per-warp counts: tile digit counts for the chained
 //     scan and tile-relative bin starts for the local reorganisation;
 //  6. thread i publishes (L, count of digit i) in the tile's status counter,
@@ -37,50 +38,74 @@
 
 namespace onesweep {
 
-template <int KBITS, bool PAIRS>
+// Tile geometries (threads per block, keys per thread, resident blocks per
+// SM). Index = the `tile_config` argument of the launcher.
+template <int KBITS, int CFG> struct TileShape;
+template <> struct TileShape<32, 0> { static constexpr int NT = 256, IPT = 24, MINB = 3; };
+template <> struct TileShape<32, 1> { static constexpr int NT = 256, IPT = 20, MINB = 3; };
+template <> struct TileShape<32, 2> { static constexpr int NT = 256, IPT = 16, MINB = 4; };
+template <> struct TileShape<32, 3> { static constexpr int NT = 512, IPT = 16, MINB = 2; };
+template <> struct TileShape<64, 0> { static constexpr int NT = 256, IPT = 12, MINB = 3; };
+template <> struct TileShape<64, 1> { static constexpr int NT = 256, IPT = 10, MINB = 3; };
+template <> struct TileShape<64, 2> { static constexpr int NT = 256, IPT = 8, MINB = 4; };
+template <> struct TileShape<64, 3> { static constexpr int NT = 512, IPT = 8, MINB = 2; };
+
+// Digit-ranking variants of step 4.
+constexpr int kRankBallot = 0;  // one ballot per digit bit (the paper's WLMS)
+constexpr int kRankSmask = 1;   // per-warp lane masks built with shared-memory atomic OR
+constexpr int kNumTileConfigs = 4;
+
+template <int KBITS, bool PAIRS, int CFG = 0>
 struct BinningConfig {
-  static constexpr int NT = 512;                        // threads per block
-  static constexpr int IPT = KBITS == 32 ? 16 : 8;      // keys per thread
-  static constexpr int MIN_BLOCKS = 2;                  // resident blocks per SM
+  static constexpr int NT = TileShape<KBITS, CFG>::NT;          // threads per block
+  static constexpr int IPT = TileShape<KBITS, CFG>::IPT;        // keys per thread
+  static constexpr int MIN_BLOCKS = TileShape<KBITS, CFG>::MINB;  // resident blocks per SM
   static constexpr int T = NT * IPT;                    // keys per tile
   static constexpr int NW = NT / 32;
   using K = typename KeyWord<KBITS>::type;
   static constexpr size_t kbuf_bytes = (size_t)T * sizeof(K);
   static constexpr size_t vbuf_bytes = PAIRS ? (size_t)T * 4 : 0;
-  static constexpr size_t whist_bytes = (size_t)NW * kRadix * 4;
+  static constexpr size_t whist_bytes = (size_t)NW * kRadix * 8;  // [NW][256] {lane mask, count}
   static constexpr size_t small_bytes = 2 * kRadix * 4 + 64 * 4 + 2 * 8;
   static constexpr size_t smem_bytes = kbuf_bytes + vbuf_bytes + whist_bytes + small_bytes;
 };
 
-// Lanes of the warp whose digit equals this lane's (valid lanes only).
-template <bool MATCH>
+// Lanes of the warp whose digit equals this lane's (valid lanes only): one
+// vote per digit bit (Section 3, WLMS), keeping the lanes that agree on it.
 __device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid, uint32_t valid_mask) {
-  if (MATCH) {
-    return __match_any_sync(0xFFFFFFFFu, valid ? d : 0xFFFFFFFFu);
-  } else {
-    // one vote per digit bit (Section 3, WLMS): keep the lanes that agree on it
-    uint32_t peers = valid_mask;
+  uint32_t peers = valid_mask;
 #pragma unroll
-    for (int b = 0; b < kRadixBits; ++b) {
-      const uint32_t v = __ballot_sync(0xFFFFFFFFu, (d >> b) & 1u);
-      const uint32_t m = 0u - ((d >> b) & 1u);  // all ones where this lane's bit is set
-      peers &= ~(v ^ m);
-    }
-    return valid ? peers : 0u;
+  for (int b = 0; b < kRadixBits; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const uint32_t v = __ballot_sync(0xFFFFFFFFu, bit);
+    peers &= bit ? v : ~v;
   }
+  return valid ? peers : 0u;
 }
 
-template <int KBITS, bool PAIRS, bool MATCH, bool FULL>
+// Float keys: FLIP bit 0 applies the sign-flip to loaded keys (first pass),
+// bit 1 undoes it on stored keys (last pass).
+template <int FLIP, typename K>
+__device__ __forceinline__ K load_transform(K k) {
+  return (FLIP & 1) ? flip_to_ordered(k) : k;
+}
+template <int FLIP, typename K>
+__device__ __forceinline__ K store_transform(K k) {
+  return (FLIP & 2) ? flip_from_ordered(k) : k;
+}
+
+template <int KBITS, bool PAIRS, int CFG, int RANK, int FLIP, bool FULL>
 __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* smem, uint32_t tile, uint32_t count,
                                              bool bulk) {
-  using C = BinningConfig<KBITS, PAIRS>;
+  using C = BinningConfig<KBITS, PAIRS, CFG>;
   using K = typename C::K;
   constexpr int NT = C::NT, IPT = C::IPT, NW = C::NW;
 
   K* kbuf = reinterpret_cast<K*>(smem);
   uint32_t* vbuf = reinterpret_cast<uint32_t*>(smem + C::kbuf_bytes);
-  uint32_t* whist = reinterpret_cast<uint32_t*>(smem + C::kbuf_bytes + C::vbuf_bytes);  // [NW][256]
-  uint32_t* dstart = whist + NW * kRadix;   // [256] tile-local start of each digit's bin
+  // [NW][256] pairs {lane mask of the current batch, running count}
+  uint32_t* whist = reinterpret_cast<uint32_t*>(smem + C::kbuf_bytes + C::vbuf_bytes);
+  uint32_t* dstart = whist + 2 * NW * kRadix;  // [256] tile-local start of each digit's bin
   uint32_t* gbase = dstart + kRadix;        // [256] global index of local position 0 of each bin
   uint32_t* misc = gbase + kRadix;          // [64] scan scratch
   uint64_t* mbar = reinterpret_cast<uint64_t*>(misc + 64);
@@ -88,7 +113,6 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int shift = a.shift;
   const uint32_t mask = a.mask;
-  const bool flip_in = a.flip_in != 0;
 
   // the next pass's status counters of this tile start at N
   if (a.status_clear && tid < kRadix) a.status_clear[(size_t)tile * kRadix + tid] = 0u;
@@ -109,12 +133,11 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
 #pragma unroll
   for (int i = 0; i < IPT; ++i) {
     const uint32_t idx = wbase + i * 32;
-    K k = (FULL || idx < count) ? kbuf[idx] : K(0);
-    key[i] = flip_in ? flip_to_ordered(k) : k;
+    key[i] = load_transform<FLIP>((FULL || idx < count) ? kbuf[idx] : K(0));
   }
 
   // 3. homogeneous-tile check
-  const K first = flip_in ? flip_to_ordered(kbuf[0]) : kbuf[0];
+  const K first = load_transform<FLIP>(kbuf[0]);
   const uint32_t d0 = digit_of(first, shift, mask);
   bool same = true;
 #pragma unroll
@@ -137,18 +160,30 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
   } else {
     // 4. warp-level multi-split ranking; rank = keys of the same digit before
     //    this one in the warp's part of the tile
-    uint32_t* wh = whist + warp * kRadix;
+    uint2* wh = reinterpret_cast<uint2*>(whist) + warp * kRadix;
     uint32_t rank2[IPT / 2];  // two 16-bit ranks per register (ranks < T <= 2^16)
+    const uint32_t lane_bit = 1u << lane;
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       const bool valid = FULL || wbase + i * 32 < count;
-      const uint32_t valid_mask = FULL ? 0xFFFFFFFFu : __ballot_sync(0xFFFFFFFFu, valid);
       const uint32_t d = digit_of(key[i], shift, mask);
-      const uint32_t peers = digit_peers<MATCH>(d, valid, valid_mask);
+      uint32_t peers, old;
+      if (RANK == kRankSmask) {
+        // every lane ORs its bit into its digit's mask word; OR commutes, so
+        // the mask read back is exactly the lanes sharing the digit
+        if (valid) atomicOr(&wh[d].x, lane_bit);
+        __syncwarp();
+        const uint2 mc = valid ? wh[d] : make_uint2(0u, 0u);
+        peers = mc.x;
+        old = mc.y;
+      } else {
+        const uint32_t valid_mask = FULL ? 0xFFFFFFFFu : __ballot_sync(0xFFFFFFFFu, valid);
+        peers = digit_peers(d, valid, valid_mask);
+        old = valid ? wh[d].y : 0u;
+      }
       const uint32_t below = __popc(peers & lanemask_lt());
-      const uint32_t old = valid ? wh[d] : 0u;
       __syncwarp();
-      if (valid && below == 0) wh[d] = old + __popc(peers);
+      if (valid && below == 0) wh[d] = make_uint2(0u, old + __popc(peers));
       __syncwarp();
       const uint32_t r = old + below;
       if (i & 1)
@@ -161,7 +196,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
     // 5. tile digit counts, publish L, per-warp exclusive offsets
     if (tid < kRadix) {
 #pragma unroll
-      for (int w = 0; w < NW; ++w) digit_count += whist[w * kRadix + tid];
+      for (int w = 0; w < NW; ++w) digit_count += whist[2 * (w * kRadix + tid) + 1];
       if (publish)
         st_relaxed_gpu(status + tid, ((tile == 0 ? kFlagGlobal : kFlagLocal) << kStatusShift) | digit_count);
     }
@@ -170,8 +205,8 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
       uint32_t run = excl;
 #pragma unroll
       for (int w = 0; w < NW; ++w) {
-        const uint32_t c = whist[w * kRadix + tid];
-        whist[w * kRadix + tid] = run;
+        const uint32_t c = whist[2 * (w * kRadix + tid) + 1];
+        whist[2 * (w * kRadix + tid) + 1] = run;
         run += c;
       }
       dstart[tid] = excl;
@@ -185,7 +220,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
     for (int i = 0; i < IPT; ++i) {
       const bool valid = FULL || wbase + i * 32 < count;
       const uint32_t r = (i & 1) ? (rank2[i / 2] >> 16) : (rank2[i / 2] & 0xFFFFu);
-      const uint32_t p = valid ? wh[digit_of(key[i], shift, mask)] + r : 0u;
+      const uint32_t p = valid ? wh[digit_of(key[i], shift, mask)].y + r : 0u;
       if (valid) kbuf[p] = key[i];
       if (PAIRS) {
         if (i & 1)
@@ -210,26 +245,34 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
     }
   }
 
-  // 6b. decoupled look-back for digit tid over the preceding tiles
+  // 6b. decoupled look-back for digit tid over the preceding tiles; the
+  //     counters of up to kWindow predecessors are read per round trip
   if (tid < kRadix) {
     uint32_t exclusive = 0;
     if (tile > 0) {
-      int64_t k = (int64_t)tile - 1;
+      constexpr int kWindow = 4;
+      int64_t k = (int64_t)tile - 1;  // nearest tile not yet accumulated
       uint32_t spins = 0;
-      while (k >= 0) {
-        const uint32_t s = ld_relaxed_gpu(a.status + (size_t)k * kRadix + tid);
-        const uint32_t flag = s >> kStatusShift;
-        if (flag == kFlagNotReady) {
-          if (++spins >= a.spin_limit) {
-            atomicOr(a.error, kErrTimeout);
-            break;
-          }
-          if ((spins & 255u) == 0 && (ld_relaxed_gpu(a.error) & kErrTimeout)) break;
-          continue;
+      bool done = false;
+      while (!done) {
+        uint32_t s[kWindow];
+#pragma unroll
+        for (int w = 0; w < kWindow; ++w)
+          s[w] = k - w >= 0 ? ld_relaxed_gpu(a.status + (size_t)(k - w) * kRadix + tid) : (kFlagGlobal << kStatusShift);
+#pragma unroll
+        for (int w = 0; w < kWindow && !done; ++w) {
+          const uint32_t flag = s[w] >> kStatusShift;
+          if (flag == kFlagNotReady) break;  // re-read from tile k next round
+          exclusive += s[w] & kValueMask;
+          --k;
+          if (flag == kFlagGlobal || k < 0) done = true;
         }
-        exclusive += s & kValueMask;
-        if (flag == kFlagGlobal) break;
-        --k;
+        if (done) break;
+        if (++spins >= a.spin_limit) {
+          atomicOr(a.error, kErrTimeout);
+          break;
+        }
+        if ((spins & 255u) == 0 && (ld_relaxed_gpu(a.error) & kErrTimeout)) break;
       }
       if (publish) st_relaxed_gpu(status + tid, (kFlagGlobal << kStatusShift) | (exclusive + digit_count));
     }
@@ -239,16 +282,13 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
 
   // 7. coalesced scatter of each local bin run to its global bin
   K* keys_out = static_cast<K*>(a.keys_out);
-  const bool flip_out = a.flip_out != 0;
   if (homogeneous) {
     const uint32_t g0 = gbase[d0];
 #pragma unroll 4
     for (int i = 0; i < IPT; ++i) {
       const uint32_t j = i * NT + tid;
       if (FULL || j < count) {
-        K k = kbuf[j];
-        if (flip_in) k = flip_to_ordered(k);
-        if (flip_out) k = flip_from_ordered(k);
+        const K k = store_transform<FLIP>(load_transform<FLIP>(kbuf[j]));
         const uint32_t g = g0 + j;
         if (g < a.n) {
           keys_out[g] = k;
@@ -264,7 +304,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
         const K k = kbuf[j];
         const uint32_t g = gbase[digit_of(k, shift, mask)] + j;
         if (g < a.n) {
-          keys_out[g] = flip_out ? flip_from_ordered(k) : k;
+          keys_out[g] = store_transform<FLIP>(k);
           if (PAIRS) a.vals_out[g] = vbuf[j];
         }
       }
@@ -272,10 +312,10 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
   }
 }
 
-template <int KBITS, bool PAIRS, bool MATCH>
-__global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS>::NT, BinningConfig<KBITS, PAIRS>::MIN_BLOCKS)
+template <int KBITS, bool PAIRS, int CFG, int RANK, int FLIP>
+__global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS, CFG>::NT, BinningConfig<KBITS, PAIRS, CFG>::MIN_BLOCKS)
     binning_kernel(PassArgs a) {
-  using C = BinningConfig<KBITS, PAIRS>;
+  using C = BinningConfig<KBITS, PAIRS, CFG>;
   using K = typename C::K;
   constexpr int NT = C::NT, T = C::T, NW = C::NW;
 
@@ -283,7 +323,7 @@ __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS>::NT, BinningConfig
   K* kbuf = reinterpret_cast<K*>(smem);
   uint32_t* vbuf = reinterpret_cast<uint32_t*>(smem + C::kbuf_bytes);
   uint32_t* whist = reinterpret_cast<uint32_t*>(smem + C::kbuf_bytes + C::vbuf_bytes);
-  uint32_t* misc = whist + NW * kRadix + 2 * kRadix;
+  uint32_t* misc = whist + 2 * NW * kRadix + 2 * kRadix;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(misc + 64);
   const int tid = threadIdx.x;
 
@@ -294,7 +334,7 @@ __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS>::NT, BinningConfig
     mbar_init(&mbar[1], 1);
     fence_mbar_init();
   }
-  for (int i = tid; i < NW * kRadix; i += NT) whist[i] = 0;
+  for (int i = tid; i < 2 * NW * kRadix; i += NT) whist[i] = 0;
   __syncthreads();
   const uint32_t tile = misc[NW + 1];
   if (tile >= a.num_tiles) return;  // only if the workspace's counters were not reset
@@ -321,25 +361,52 @@ __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS>::NT, BinningConfig
   }
 
   if (full)
-    binning_tile<KBITS, PAIRS, MATCH, true>(a, smem, tile, count, bulk);
+    binning_tile<KBITS, PAIRS, CFG, RANK, FLIP, true>(a, smem, tile, count, bulk);
   else
-    binning_tile<KBITS, PAIRS, MATCH, false>(a, smem, tile, count, bulk);
+    binning_tile<KBITS, PAIRS, CFG, RANK, FLIP, false>(a, smem, tile, count, bulk);
+}
+
+template <int KBITS, bool PAIRS, int CFG, int RANK, int FLIP>
+cudaError_t launch_binning_one(const PassArgs& a, cudaStream_t s) {
+  using C = BinningConfig<KBITS, PAIRS, CFG>;
+  static int configured_device = -1;  // one attribute call per device switch
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_device != dev) {
+    cudaError_t e = cudaFuncSetAttribute(binning_kernel<KBITS, PAIRS, CFG, RANK, FLIP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bytes);
+    if (e != cudaSuccess) return e;
+    configured_device = dev;
+  }
+  binning_kernel<KBITS, PAIRS, CFG, RANK, FLIP><<<a.num_tiles, C::NT, C::smem_bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int KBITS, bool PAIRS, int FLIP, int RANK>
+cudaError_t launch_binning_flip_rank(const PassArgs& a, cudaStream_t s, int cfg) {
+  switch (cfg) {
+    case 1: return launch_binning_one<KBITS, PAIRS, 1, RANK, FLIP>(a, s);
+    case 2: return launch_binning_one<KBITS, PAIRS, 2, RANK, FLIP>(a, s);
+    case 3: return launch_binning_one<KBITS, PAIRS, 3, RANK, FLIP>(a, s);
+    default: return launch_binning_one<KBITS, PAIRS, 0, RANK, FLIP>(a, s);
+  }
+}
+
+// All tile geometries and both ranking variants for one (width, payload, flip).
+template <int KBITS, bool PAIRS, int FLIP>
+cudaError_t launch_binning_flip(const PassArgs& a, cudaStream_t s, int cfg, int rank) {
+  return rank == kRankSmask ? launch_binning_flip_rank<KBITS, PAIRS, FLIP, kRankSmask>(a, s, cfg)
+                            : launch_binning_flip_rank<KBITS, PAIRS, FLIP, kRankBallot>(a, s, cfg);
 }
 
 template <int KBITS, bool PAIRS>
-cudaError_t launch_binning_t(const PassArgs& a, cudaStream_t s, bool match) {
-  using C = BinningConfig<KBITS, PAIRS>;
-  static int configured_device[2] = {-1, -1};  // one attribute call per device switch
-  int dev = 0;
-  cudaGetDevice(&dev);
-  auto kern = match ? binning_kernel<KBITS, PAIRS, true> : binning_kernel<KBITS, PAIRS, false>;
-  if (configured_device[match] != dev) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bytes);
-    if (e != cudaSuccess) return e;
-    configured_device[match] = dev;
+uint32_t tile_keys_t(int cfg) {
+  switch (cfg) {
+    case 1: return BinningConfig<KBITS, PAIRS, 1>::T;
+    case 2: return BinningConfig<KBITS, PAIRS, 2>::T;
+    case 3: return BinningConfig<KBITS, PAIRS, 3>::T;
+    default: return BinningConfig<KBITS, PAIRS, 0>::T;
   }
-  kern<<<a.num_tiles, C::NT, C::smem_bytes, s>>>(a);
-  return cudaGetLastError();
 }
 
 }  // namespace onesweep

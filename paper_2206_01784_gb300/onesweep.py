@@ -75,6 +75,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.os_status_string.argtypes = [i32]
     lib.os_debug_set_lookback_fault.restype = None
     lib.os_debug_set_lookback_fault.argtypes = [i64, u32]
+    lib.os_num_tile_configs.restype = i32
+    lib.os_num_tile_configs.argtypes = []
+    lib.os_tile_config_keys.restype = i32
+    lib.os_tile_config_keys.argtypes = [i32, i32, i32]
+    lib.os_set_tile_config.restype = i32
+    lib.os_set_tile_config.argtypes = [i32, i32, i32]
+    lib.os_get_tile_config.restype = i32
+    lib.os_get_tile_config.argtypes = [i32, i32]
     lib.os_profile_start.restype = i32
     lib.os_profile_start.argtypes = [i32]
     lib.os_profile_stop.restype = i32
@@ -126,6 +134,22 @@ def os_status_string(status: int) -> str:
 
 def os_debug_set_lookback_fault(tile: int, spin_limit: int = 0) -> None:
     load().os_debug_set_lookback_fault(tile, spin_limit)
+
+
+def os_num_tile_configs() -> int:
+    return int(load().os_num_tile_configs())
+
+
+def os_tile_config_keys(key_bits: int, value_bytes: int, cfg: int) -> int:
+    return int(load().os_tile_config_keys(key_bits, value_bytes, cfg))
+
+
+def os_set_tile_config(key_bits: int, value_bytes: int, cfg: int) -> int:
+    return int(load().os_set_tile_config(key_bits, value_bytes, cfg))
+
+
+def os_get_tile_config(key_bits: int, value_bytes: int) -> int:
+    return int(load().os_get_tile_config(key_bits, value_bytes))
 
 
 def os_profile_start(capacity: int) -> int:

@@ -96,3 +96,22 @@ def test_status_strings():
     for s in range(6):
         assert osw.os_status_string(s)
     assert "2^30" in osw.os_status_string(osw.OS_ERR_TOO_LARGE)
+
+
+def test_tile_configs_host_side():
+    n_cfg = osw.os_num_tile_configs()
+    assert n_cfg >= 1
+    for kb in (32, 64):
+        for vb in (0, 4):
+            sizes = [osw.os_tile_config_keys(kb, vb, c) for c in range(n_cfg)]
+            assert all(t >= 256 for t in sizes)
+            ws = osw.os_sort_workspace_bytes(osw.OS_KEY_U32 if kb == 32 else osw.OS_KEY_U64, 1_000_000, vb, 0, kb)
+            for c in range(n_cfg):
+                assert osw.os_set_tile_config(kb, vb, c) == osw.OS_OK
+                assert osw.os_get_tile_config(kb, vb) == c
+                lay = osw.os_sort_workspace_layout(osw.OS_KEY_U32 if kb == 32 else osw.OS_KEY_U64, 1_000_000, vb, 0, kb)
+                assert lay.total_bytes == ws and lay.tile_keys == sizes[c]
+            osw.os_set_tile_config(kb, vb, 0)
+    assert osw.os_set_tile_config(32, 0, n_cfg) == osw.OS_ERR_INVALID_ARG
+    assert osw.os_set_tile_config(16, 0, 0) == osw.OS_ERR_INVALID_ARG
+    assert osw.os_tile_config_keys(32, 3, 0) == 0

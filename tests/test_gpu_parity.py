@@ -259,3 +259,27 @@ def test_lookback_wait_limit_reports_timeout():
     assert rc == osw.OS_OK
     assert osw.os_workspace_status(ws.data_ptr(), s) == osw.OS_OK
     assert np.array_equal(to_host(out, np.uint32), oracle.sort("u32", keys))
+
+
+@pytest.mark.parametrize("cfg", list(range(8)))
+@pytest.mark.parametrize("kt", ["u32", "u64", "f32"])
+def test_every_tile_config(cfg, kt):
+    # every binning tile geometry gives the oracle's result (workspaces are
+    # sized for the smallest tile, so the same sizing serves all of them)
+    kb = KB[kt]
+    try:
+        for pairs in (False, True):
+            assert osw.os_set_tile_config(kb, 4 if pairs else 0, cfg) == osw.OS_OK
+            t = osw.os_tile_config_keys(kb, 4 if pairs else 0, cfg)
+            for n in (t - 1, 2 * t, 5 * t + 3):
+                keys = make_keys(kt, "and2" if kt != "f32" else "normal", n, seed=cfg * 7 + n)
+                vals = workload.iota_u32(n) if pairs else None
+                got = gpu_sort(kt, keys, vals)
+                exp = oracle.sort(kt, keys, vals)
+                if pairs:
+                    assert np.array_equal(got[0], exp[0]) and np.array_equal(got[1], exp[1]), (cfg, n)
+                else:
+                    assert np.array_equal(got, exp), (cfg, n)
+    finally:
+        for vb in (0, 4):
+            osw.os_set_tile_config(kb, vb, 0)
