@@ -117,6 +117,27 @@ OS_API int os_sort_pairs(int key_type, const void *keys_in, void *keys_out, cons
                   uint64_t n, int begin_bit, int end_bit, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Segmented (batched) sort: num_segments independent arrays held back to
+ * back, segment s = [seg_offsets[s], seg_offsets[s+1]), each sorted on its
+ * own, in one call of a few launches whatever the number of segments (each
+ * segment gets its own Section 3 histograms, bin offsets and look-back
+ * chain; segments of up to one block's capacity are sorted in shared
+ * memory). seg_offsets: num_segments + 1 uint64 (DEVICE), nondecreasing,
+ * seg_offsets[num_segments] <= n_total, each segment shorter than 2^30 keys;
+ * keys outside every segment are not written. n_total < 2^31. The offsets
+ * are read on the device only, so a call can be captured in a CUDA graph;
+ * invalid offsets are reported by os_workspace_status() as
+ * OS_ERR_INVALID_ARG (nothing is sorted). vals_in / vals_out: NULL for keys
+ * only, else n_total uint32 each. ws: os_sort_batch_workspace_bytes() bytes.
+ * Not part of the paper: the batching the paper's single sort is built into.
+ */
+OS_API size_t os_sort_batch_workspace_bytes(int key_type, uint64_t n_total, int num_segments, int value_bytes,
+                                            int begin_bit, int end_bit);
+OS_API int os_sort_batch(int key_type, const void *keys_in, void *keys_out, const uint32_t *vals_in,
+                         uint32_t *vals_out, const uint64_t *seg_offsets, int num_segments, uint64_t n_total,
+                         int begin_bit, int end_bit, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * Phases 1 and 2 only (Section 3, "Upfront histogram kernel" and
  * "Exclusive sum kernel"): the digit counts of every place of the n keys and
  * their exclusive prefix sums. hist_out and offsets_out are device arrays of
@@ -172,7 +193,8 @@ OS_API void os_debug_set_lookback_fault(int64_t tile, uint32_t spin_limit);
  * recording off. Process-wide, not thread-safe. Both return an os_status.
  */
 typedef struct {
-    int kernel;   /* 0 = histogram (phases 1-2), 1 = digit binning (phase 3) */
+    int kernel;   /* 0 = histogram (phases 1-2), 1 = digit binning (phase 3),
+                     2 = batch plan, 3 = batch one-block sort of small segments */
     int pass;     /* digit place of a binning launch, -1 for the histogram */
     float ms;     /* device time between the pair of events */
 } os_launch_time;

@@ -17,26 +17,34 @@
 
 namespace onesweep {
 
-#define OS_DECLARE_BINNING(KB, PR)                                                        \
-  cudaError_t launch_binning##KB##_##PR##_f0(int, int, const PassArgs&, cudaStream_t);   \
-  cudaError_t launch_binning##KB##_##PR##_f1(int, int, const PassArgs&, cudaStream_t);   \
-  cudaError_t launch_binning##KB##_##PR##_f2(int, int, const PassArgs&, cudaStream_t);   \
-  cudaError_t launch_binning##KB##_##PR##_f3(int, int, const PassArgs&, cudaStream_t);   \
+#define OS_DECLARE_BINNING_MODE(KB, PR, M)                                                  \
+  cudaError_t launch_binning##KB##_##PR##_f0_##M(int, int, const PassArgs&, cudaStream_t);   \
+  cudaError_t launch_binning##KB##_##PR##_f1_##M(int, int, const PassArgs&, cudaStream_t);   \
+  cudaError_t launch_binning##KB##_##PR##_f2_##M(int, int, const PassArgs&, cudaStream_t);   \
+  cudaError_t launch_binning##KB##_##PR##_f3_##M(int, int, const PassArgs&, cudaStream_t);
+#define OS_DECLARE_BINNING(KB, PR)           \
+  OS_DECLARE_BINNING_MODE(KB, PR, single)    \
+  OS_DECLARE_BINNING_MODE(KB, PR, seg)       \
   uint32_t binning_tile_keys##KB##_##PR(int cfg);
 OS_DECLARE_BINNING(32, pairs)
 OS_DECLARE_BINNING(32, keys)
 OS_DECLARE_BINNING(64, pairs)
 OS_DECLARE_BINNING(64, keys)
 #undef OS_DECLARE_BINNING
+#undef OS_DECLARE_BINNING_MODE
 
 using BinningLaunch = cudaError_t (*)(int, int, const PassArgs&, cudaStream_t);
 
-// [64-bit][pairs][float transform mode]
-const BinningLaunch kBinningLaunch[2][2][4] = {
-    {{launch_binning32_keys_f0, launch_binning32_keys_f1, launch_binning32_keys_f2, launch_binning32_keys_f3},
-     {launch_binning32_pairs_f0, launch_binning32_pairs_f1, launch_binning32_pairs_f2, launch_binning32_pairs_f3}},
-    {{launch_binning64_keys_f0, launch_binning64_keys_f1, launch_binning64_keys_f2, launch_binning64_keys_f3},
-     {launch_binning64_pairs_f0, launch_binning64_pairs_f1, launch_binning64_pairs_f2, launch_binning64_pairs_f3}}};
+#define OS_BINNING_ROW(KB, PR, M) \
+  {launch_binning##KB##_##PR##_f0_##M, launch_binning##KB##_##PR##_f1_##M, launch_binning##KB##_##PR##_f2_##M, \
+   launch_binning##KB##_##PR##_f3_##M}
+// [segmented][64-bit][pairs][float transform mode]
+const BinningLaunch kBinningLaunch[2][2][2][4] = {
+    {{OS_BINNING_ROW(32, keys, single), OS_BINNING_ROW(32, pairs, single)},
+     {OS_BINNING_ROW(64, keys, single), OS_BINNING_ROW(64, pairs, single)}},
+    {{OS_BINNING_ROW(32, keys, seg), OS_BINNING_ROW(32, pairs, seg)},
+     {OS_BINNING_ROW(64, keys, seg), OS_BINNING_ROW(64, pairs, seg)}}};
+#undef OS_BINNING_ROW
 
 // Binning kernel variants: tile geometry (4) x digit-ranking method (2);
 // variant v uses geometry v % 4 and ranking v / 4 (0: one ballot per digit
@@ -45,8 +53,10 @@ constexpr int kGeometries = 4;
 constexpr int kTileConfigs = 2 * kGeometries;
 
 // Active variant per (key width, keys only / pairs); set by
-// os_set_tile_config (the autotuner's hook).
-int g_tile_cfg[2][2] = {{0, 0}, {0, 0}};
+// os_set_tile_config (the autotuner's hook). Default: geometry 0 with
+// shared-memory lane masks (the fastest measured on GB300).
+constexpr int kDefaultTileConfig = kGeometries + 0;
+int g_tile_cfg[2][2] = {{kDefaultTileConfig, kDefaultTileConfig}, {kDefaultTileConfig, kDefaultTileConfig}};
 
 uint32_t tile_keys_for(int key_bits, bool pairs, int cfg) {
   const int geo = cfg % kGeometries;
@@ -72,7 +82,8 @@ uint32_t min_tile_keys(int key_bits, bool pairs) {
 cudaError_t launch_binning(int key_bits, bool pairs, const PassArgs& a, cudaStream_t s) {
   const int cfg = g_tile_cfg[key_bits == 64][pairs];
   const int flip = (a.flip_in ? 1 : 0) | (a.flip_out ? 2 : 0);
-  return kBinningLaunch[key_bits == 64][pairs][flip](cfg % kGeometries, cfg / kGeometries, a, s);
+  const int seg = a.seg_offsets != nullptr;
+  return kBinningLaunch[seg][key_bits == 64][pairs][flip](cfg % kGeometries, cfg / kGeometries, a, s);
 }
 
 namespace {
@@ -319,6 +330,201 @@ int run_sort(int key_type, const void* keys_in, void* keys_out, const uint32_t* 
   return OS_OK;
 }
 
+// ---------------------------------------------------------------- batches
+
+constexpr uint32_t kHistChunk = 32768;         // keys per histogram work item of a batch
+constexpr uint64_t kMaxBatchKeys = 1ull << 31;  // total keys of a batch (32-bit indices)
+constexpr uint64_t kMaxSegments = 1ull << 24;
+
+// Batch header words (same header as a single sort): 0 status, 2 binning
+// tiles, 3 histogram items, 4 invalid-offsets flag, 16.. tile counters.
+constexpr size_t kTotalsWord = 2;
+
+struct BatchPlan {
+  int key_bits = 0;
+  bool pairs = false;
+  int places = 0;
+  uint32_t tile = 0, small_max = 0;
+  uint64_t max_tiles = 0, max_items = 0;
+  size_t seg_done = 0, seg_hist = 0, zero_end = 0, seg_bin_offsets = 0, tile_base = 0, hist_base = 0;
+  size_t tile_seg = 0, hist_seg = 0, status[2] = {0, 0}, alt_keys = 0, alt_vals = 0, total = 0;
+};
+
+int make_batch_plan(int key_type, uint64_t n_total, int64_t num_segments, int value_bytes, int begin_bit,
+                    int end_bit, BatchPlan* bp) {
+  const int kb = key_bits_of(key_type);
+  if (kb == 0 || num_segments < 0) return OS_ERR_INVALID_ARG;
+  if (value_bytes != 0 && value_bytes != 4) return OS_ERR_INVALID_ARG;
+  if (begin_bit < 0 || end_bit > kb || begin_bit > end_bit) return OS_ERR_INVALID_ARG;
+  if (n_total >= kMaxBatchKeys || (uint64_t)num_segments > kMaxSegments) return OS_ERR_TOO_LARGE;
+  const uint64_t S = (uint64_t)num_segments;
+  bp->key_bits = kb;
+  bp->pairs = value_bytes == 4;
+  bp->places = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
+  bp->tile = binning_tile_keys(kb, bp->pairs);
+  bp->small_max = batch_local_capacity(kb, bp->pairs);
+  const uint32_t min_tile = min_tile_keys(kb, bp->pairs);
+  bp->max_tiles = (n_total + min_tile - 1) / min_tile + S;
+  bp->max_items = (n_total + kHistChunk - 1) / kHistChunk + S;
+  const size_t per_seg = (size_t)(bp->places > 0 ? bp->places : 1) * kRadix * 4;
+  size_t off = kHeaderBytes;
+  bp->seg_done = off;
+  off = round_up(off + S * 4);
+  bp->seg_hist = off;
+  off = round_up(off + S * per_seg);
+  bp->zero_end = off;
+  bp->seg_bin_offsets = off;
+  off = round_up(off + S * per_seg);
+  bp->tile_base = off;
+  off = round_up(off + (S + 1) * 4);
+  bp->hist_base = off;
+  off = round_up(off + (S + 1) * 4);
+  bp->tile_seg = off;
+  off = round_up(off + bp->max_tiles * 4);
+  bp->hist_seg = off;
+  off = round_up(off + bp->max_items * 4);
+  const size_t slab = (size_t)bp->max_tiles * kRadix * 4;
+  bp->status[0] = off;
+  off = round_up(off + slab);
+  bp->status[1] = off;
+  off = round_up(off + (bp->places > 1 ? slab : 0));
+  bp->alt_keys = off;
+  off = round_up(off + (bp->places > 1 ? (size_t)n_total * (kb / 8) : 0));
+  bp->alt_vals = off;
+  off = round_up(off + (bp->places > 1 && bp->pairs ? (size_t)n_total * 4 : 0));
+  bp->total = off;
+  return OS_OK;
+}
+
+int run_batch(int key_type, const void* keys_in, void* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
+              const uint64_t* seg_offsets, int64_t num_segments, uint64_t n_total, int begin_bit, int end_bit,
+              void* ws, size_t ws_bytes, void* stream) {
+  const bool pairs = vals_in != nullptr || vals_out != nullptr;
+  if (pairs && (vals_in == nullptr || vals_out == nullptr)) return OS_ERR_INVALID_ARG;
+  BatchPlan bp;
+  int rc = make_batch_plan(key_type, n_total, num_segments, pairs ? 4 : 0, begin_bit, end_bit, &bp);
+  if (rc != OS_OK) return rc;
+  if (n_total == 0 || num_segments == 0) return OS_OK;
+  const size_t kbytes = (size_t)n_total * (bp.key_bits / 8);
+  const size_t vbytes = pairs ? (size_t)n_total * 4 : 0;
+  if (!keys_in || !keys_out || !seg_offsets) return OS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(keys_in) % (bp.key_bits / 8) ||
+      reinterpret_cast<uintptr_t>(keys_out) % (bp.key_bits / 8) || reinterpret_cast<uintptr_t>(seg_offsets) % 8)
+    return OS_ERR_INVALID_ARG;
+  if (pairs && (reinterpret_cast<uintptr_t>(vals_in) % 4 || reinterpret_cast<uintptr_t>(vals_out) % 4))
+    return OS_ERR_INVALID_ARG;
+  if (!ws || ws_bytes < bp.total) return OS_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(ws) % 16) return OS_ERR_INVALID_ARG;
+  {
+    const void* bufs[5] = {keys_in, keys_out, vals_in, vals_out, ws};
+    const size_t sizes[5] = {kbytes, kbytes, vbytes, vbytes, bp.total};
+    for (int i = 0; i < 5; ++i)
+      for (int j = i + 1; j < 5; ++j)
+        if (overlaps(bufs[i], sizes[i], bufs[j], sizes[j])) return OS_ERR_INVALID_ARG;
+    if (overlaps(seg_offsets, ((size_t)num_segments + 1) * 8, keys_out, kbytes) ||
+        overlaps(seg_offsets, ((size_t)num_segments + 1) * 8, vals_out, vbytes) ||
+        overlaps(seg_offsets, ((size_t)num_segments + 1) * 8, ws, bp.total))
+      return OS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  uint32_t* header = reinterpret_cast<uint32_t*>(w);
+
+  if (bp.places == 0) {  // empty bit range: a plain copy
+    if (cudaMemsetAsync(w, 0, 4, s) != cudaSuccess) return OS_ERR_CUDA;
+    if (cudaMemcpyAsync(keys_out, keys_in, kbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return OS_ERR_CUDA;
+    if (pairs && cudaMemcpyAsync(vals_out, vals_in, vbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return OS_ERR_CUDA;
+    return OS_OK;
+  }
+  if (cudaMemsetAsync(w, 0, bp.zero_end, s) != cudaSuccess) return OS_ERR_CUDA;
+
+  BatchArgs b{};
+  b.keys_in = keys_in;
+  b.keys_out = keys_out;
+  b.vals_in = vals_in;
+  b.vals_out = vals_out;
+  b.seg_offsets = seg_offsets;
+  b.num_segments = (uint32_t)num_segments;
+  b.n_total = n_total;
+  b.flip = is_float(key_type);
+  b.num_places = bp.places;
+  b.begin_bit = begin_bit;
+  b.end_bit = end_bit;
+  b.small_max = bp.small_max;
+  b.tile_keys = bp.tile;
+  b.hist_chunk = kHistChunk;
+  b.max_tiles = (uint32_t)bp.max_tiles;
+  b.max_items = (uint32_t)bp.max_items;
+  b.tile_base = reinterpret_cast<uint32_t*>(w + bp.tile_base);
+  b.tile_seg = reinterpret_cast<uint32_t*>(w + bp.tile_seg);
+  b.hist_base = reinterpret_cast<uint32_t*>(w + bp.hist_base);
+  b.hist_seg = reinterpret_cast<uint32_t*>(w + bp.hist_seg);
+  b.totals = header + kTotalsWord;
+  b.seg_done = reinterpret_cast<uint32_t*>(w + bp.seg_done);
+  b.seg_hist = reinterpret_cast<uint32_t*>(w + bp.seg_hist);
+  b.seg_bin_offsets = reinterpret_cast<uint32_t*>(w + bp.seg_bin_offsets);
+  b.error = header;
+  b.clear = reinterpret_cast<uint32_t*>(w + bp.status[0]);
+  b.clear_words = bp.max_tiles * kRadix;
+
+  int slot = prof_begin(2, -1, s);
+  cudaError_t e = launch_batch_plan(b, s);
+  prof_end(slot, s);
+  if (e != cudaSuccess) return OS_ERR_CUDA;
+  slot = prof_begin(0, -1, s);
+  e = launch_batch_histogram(bp.key_bits, b, s);
+  prof_end(slot, s);
+  if (e != cudaSuccess) return OS_ERR_CUDA;
+  slot = prof_begin(3, -1, s);
+  e = launch_batch_local_sort(bp.key_bits, pairs, b, s);
+  prof_end(slot, s);
+  if (e != cudaSuccess) return OS_ERR_CUDA;
+
+  void* alt_keys = w + bp.alt_keys;
+  uint32_t* alt_vals = reinterpret_cast<uint32_t*>(w + bp.alt_vals);
+  auto aligned16 = [](const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
+  const void* src_k = keys_in;
+  const uint32_t* src_v = vals_in;
+  for (int pass = 0; pass < bp.places; ++pass) {
+    const bool to_out = ((bp.places - 1 - pass) % 2) == 0;
+    void* dst_k = to_out ? keys_out : alt_keys;
+    uint32_t* dst_v = to_out ? vals_out : alt_vals;
+    PassArgs a{};
+    a.keys_in = src_k;
+    a.keys_out = dst_k;
+    a.vals_in = pairs ? src_v : nullptr;
+    a.vals_out = pairs ? dst_v : nullptr;
+    a.n = (uint32_t)n_total;
+    a.num_tiles = (uint32_t)bp.max_tiles;
+    a.shift = begin_bit + kRadixBits * pass;
+    const int width = end_bit - a.shift < kRadixBits ? end_bit - a.shift : kRadixBits;
+    a.mask = (1u << width) - 1u;
+    a.flip_in = is_float(key_type) && pass == 0;
+    a.flip_out = is_float(key_type) && pass == bp.places - 1;
+    a.use_bulk = aligned16(src_k) && (!pairs || aligned16(src_v));
+    a.bin_offsets = b.seg_bin_offsets + pass * kRadix;
+    a.offsets_stride = (uint32_t)bp.places * kRadix;
+    a.status = reinterpret_cast<uint32_t*>(w + bp.status[pass & 1]);
+    a.status_clear = pass + 1 < bp.places ? reinterpret_cast<uint32_t*>(w + bp.status[(pass + 1) & 1]) : nullptr;
+    a.tile_counter = header + kTileCounterWord + pass % 8;
+    a.error = header;
+    a.spin_limit = g_spin_limit;
+    a.fault_tile = g_fault_tile;
+    a.seg_offsets = seg_offsets;
+    a.tile_base = b.tile_base;
+    a.tile_seg = b.tile_seg;
+    a.total_tiles = b.totals;
+    slot = prof_begin(1, pass, s);
+    e = launch_binning(bp.key_bits, pairs, a, s);
+    prof_end(slot, s);
+    if (e != cudaSuccess) return OS_ERR_CUDA;
+    src_k = dst_k;
+    src_v = dst_v;
+  }
+  return OS_OK;
+}
+
 }  // namespace
 }  // namespace onesweep
 
@@ -351,6 +557,20 @@ int os_sort_pairs(int key_type, const void* keys_in, void* keys_out, const uint3
                   uint64_t n, int begin_bit, int end_bit, void* ws, size_t ws_bytes, void* stream) {
   if (!vals_in || !vals_out) return OS_ERR_INVALID_ARG;
   return run_sort(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws, ws_bytes, stream);
+}
+
+size_t os_sort_batch_workspace_bytes(int key_type, uint64_t n_total, int num_segments, int value_bytes,
+                                     int begin_bit, int end_bit) {
+  BatchPlan bp;
+  if (make_batch_plan(key_type, n_total, num_segments, value_bytes, begin_bit, end_bit, &bp) != OS_OK) return 0;
+  return bp.total;
+}
+
+int os_sort_batch(int key_type, const void* keys_in, void* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
+                  const uint64_t* seg_offsets, int num_segments, uint64_t n_total, int begin_bit, int end_bit, void* ws,
+                  size_t ws_bytes, void* stream) {
+  return run_batch(key_type, keys_in, keys_out, vals_in, vals_out, seg_offsets, num_segments, n_total, begin_bit,
+                   end_bit, ws, ws_bytes, stream);
 }
 
 int os_digit_histograms(int key_type, const void* keys_in, uint64_t n, int begin_bit, int end_bit,
@@ -387,6 +607,7 @@ int os_workspace_status(const void* ws, void* stream) {
   if (cudaStreamSynchronize(s) != cudaSuccess) return OS_ERR_CUDA;
   uint32_t word = 0;
   if (cudaMemcpy(&word, ws, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return OS_ERR_CUDA;
+  if (word & kErrBadSegments) return OS_ERR_INVALID_ARG;
   if (word & kErrTimeout) return OS_ERR_TIMEOUT;
   return OS_OK;
 }

@@ -1,0 +1,14 @@
+// Instantiations of the digit-binning kernel: 32-bit keys, pairs, float
+// transform mode 0 (bit 0: sign-flip on load, bit 1: undo on store),
+// one array.
+#include "os_binning.cuh"
+
+namespace onesweep {
+
+cudaError_t launch_binning32_pairs_f0_single(int cfg, int rank, const PassArgs& a, cudaStream_t s) {
+  return launch_binning_flip<32, true, 0, false>(a, s, cfg, rank);
+}
+
+uint32_t binning_tile_keys32_pairs(int cfg) { return tile_keys_t<32, true>(cfg); }
+
+}  // namespace onesweep

@@ -1,0 +1,12 @@
+// Instantiations of the digit-binning kernel: 64-bit keys, keys, float
+// transform mode 1 (bit 0: sign-flip on load, bit 1: undo on store),
+// segmented (batch) mode.
+#include "os_binning.cuh"
+
+namespace onesweep {
+
+cudaError_t launch_binning64_keys_f1_seg(int cfg, int rank, const PassArgs& a, cudaStream_t s) {
+  return launch_binning_flip<64, false, 1, true>(a, s, cfg, rank);
+}
+
+}  // namespace onesweep

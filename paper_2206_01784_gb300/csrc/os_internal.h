@@ -43,7 +43,55 @@ struct PassArgs {
   uint32_t* error;           // device status word
   uint32_t spin_limit;       // look-back polls before giving up
   int64_t fault_tile;        // test hook: tile that never publishes (-1 = none)
+
+  // Segmented mode (os_sort_batch); seg_offsets == nullptr means one array of
+  // n keys. Each segment is its own sort: its tiles form one look-back chain
+  // and it has its own bin offsets.
+  const uint64_t* seg_offsets;   // [S+1] segment boundaries (device)
+  const uint32_t* tile_base;     // [S+1] first tile of each segment's chain
+  const uint32_t* tile_seg;      // [tiles] segment of each tile
+  const uint32_t* total_tiles;   // device word: tiles in this pass
+  uint32_t offsets_stride;       // words between two segments' bin offsets
 };
+
+// Segmented sort: the plan, per-segment histograms and the one-block sort of
+// small segments (os_batch.cu).
+struct BatchArgs {
+  const void* keys_in;
+  void* keys_out;
+  const uint32_t* vals_in;
+  uint32_t* vals_out;
+  const uint64_t* seg_offsets;   // [S+1]
+  uint32_t num_segments;
+  uint64_t n_total;
+  int flip;                      // float keys
+  int num_places;
+  int begin_bit;
+  int end_bit;
+  uint32_t small_max;            // segments up to this length are sorted in one block
+  uint32_t tile_keys;            // binning tile of the large segments
+  uint32_t hist_chunk;           // keys per histogram work item
+  uint32_t max_tiles;            // capacity of tile_seg
+  uint32_t max_items;            // capacity of hist_seg
+  uint32_t* tile_base;           // [S+1]
+  uint32_t* tile_seg;            // [max_tiles]
+  uint32_t* hist_base;           // [S+1]
+  uint32_t* hist_seg;            // [max_items]
+  uint32_t* totals;              // [0] binning tiles, [1] histogram items
+  uint32_t* seg_done;            // [S] zeroed
+  uint32_t* seg_hist;            // [S][p][256] zeroed
+  uint32_t* seg_bin_offsets;     // [S][p][256]
+  uint32_t* error;
+  uint32_t* clear;               // status slab of the first pass, to zero
+  uint64_t clear_words;
+};
+
+constexpr uint32_t kErrBadSegments = 2u;  // device status word bit: invalid segment offsets
+
+cudaError_t launch_batch_plan(const BatchArgs& b, cudaStream_t s);
+cudaError_t launch_batch_histogram(int key_bits, const BatchArgs& b, cudaStream_t s);
+cudaError_t launch_batch_local_sort(int key_bits, bool pairs, const BatchArgs& b, cudaStream_t s);
+uint32_t batch_local_capacity(int key_bits, bool pairs);
 
 // Tile geometry of the binning kernel for a key width / payload combination.
 uint32_t binning_tile_keys(int key_bits, bool pairs);

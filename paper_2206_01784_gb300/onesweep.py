@@ -67,6 +67,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.os_sort_keys.argtypes = [i32, vp, vp, u64, i32, i32, vp, sz, vp]
     lib.os_sort_pairs.restype = i32
     lib.os_sort_pairs.argtypes = [i32, vp, vp, vp, vp, u64, i32, i32, vp, sz, vp]
+    lib.os_sort_batch_workspace_bytes.restype = sz
+    lib.os_sort_batch_workspace_bytes.argtypes = [i32, u64, i32, i32, i32, i32]
+    lib.os_sort_batch.restype = i32
+    lib.os_sort_batch.argtypes = [i32, vp, vp, vp, vp, vp, i32, u64, i32, i32, vp, sz, vp]
     lib.os_digit_histograms.restype = i32
     lib.os_digit_histograms.argtypes = [i32, vp, u64, i32, i32, vp, vp, vp, sz, vp]
     lib.os_workspace_status.restype = i32
@@ -113,6 +117,17 @@ def os_sort_pairs(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, 
                   stream) -> int:
     return int(load().os_sort_pairs(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws,
                                     ws_bytes, stream))
+
+
+def os_sort_batch_workspace_bytes(key_type: int, n_total: int, num_segments: int, value_bytes: int, begin_bit: int,
+                                  end_bit: int) -> int:
+    return int(load().os_sort_batch_workspace_bytes(key_type, n_total, num_segments, value_bytes, begin_bit, end_bit))
+
+
+def os_sort_batch(key_type, keys_in, keys_out, vals_in, vals_out, seg_offsets, num_segments, n_total, begin_bit,
+                  end_bit, ws, ws_bytes, stream) -> int:
+    return int(load().os_sort_batch(key_type, keys_in, keys_out, vals_in, vals_out, seg_offsets, num_segments,
+                                    n_total, begin_bit, end_bit, ws, ws_bytes, stream))
 
 
 def os_digit_histograms(key_type, keys_in, n, begin_bit, end_bit, hist_out, offsets_out, ws, ws_bytes,
@@ -255,3 +270,41 @@ def digit_histograms(keys, begin_bit: int = 0, end_bit: int | None = None, key_t
     _check(os_digit_histograms(kt, keys.data_ptr(), n, begin_bit, end_bit, hist.data_ptr(), offs.data_ptr(),
                                ws.data_ptr(), ws.numel(), _stream_ptr(stream)), "os_digit_histograms")
     return hist, offs
+
+
+def batch_workspace(key_type: int, n_total: int, num_segments: int, value_bytes: int, begin_bit: int, end_bit: int,
+                    device):
+    torch = _torch()
+    nbytes = os_sort_batch_workspace_bytes(key_type, n_total, num_segments, value_bytes, begin_bit, end_bit)
+    if nbytes == 0:
+        raise OnesweepError(OS_ERR_INVALID_ARG, "os_sort_batch_workspace_bytes")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def sort_batch(keys, seg_offsets, values=None, begin_bit: int = 0, end_bit: int | None = None, key_type=None,
+               keys_out=None, values_out=None, ws=None, stream=None):
+    """Sorts each segment [seg_offsets[s], seg_offsets[s+1]) of a 1-D CUDA
+    tensor on its own. seg_offsets: int64 CUDA tensor of num_segments + 1
+    boundaries. Returns keys (or (keys, values))."""
+    torch = _torch()
+    kt = key_type_of(keys, key_type)
+    end_bit = KEY_BITS[kt] if end_bit is None else end_bit
+    keys = keys.contiguous()
+    offs = seg_offsets.contiguous()
+    if offs.dtype not in (torch.int64, torch.uint64) or offs.device != keys.device:
+        raise ValueError("seg_offsets must be an int64 tensor on the keys' device")
+    n = keys.numel()
+    segs = offs.numel() - 1
+    keys_out = torch.empty_like(keys) if keys_out is None else keys_out
+    vb = 0
+    vin = vout = None
+    if values is not None:
+        values = values.contiguous()
+        if values.element_size() != 4 or values.numel() != n:
+            raise ValueError("values must be a 4-byte tensor with one value per key")
+        values_out = torch.empty_like(values) if values_out is None else values_out
+        vb, vin, vout = 4, values.data_ptr(), values_out.data_ptr()
+    ws = batch_workspace(kt, n, segs, vb, begin_bit, end_bit, keys.device) if ws is None else ws
+    _check(os_sort_batch(kt, keys.data_ptr(), keys_out.data_ptr(), vin, vout, offs.data_ptr(), segs, n, begin_bit,
+                         end_bit, ws.data_ptr(), ws.numel(), _stream_ptr(stream)), "os_sort_batch")
+    return keys_out if values is None else (keys_out, values_out)

@@ -106,12 +106,34 @@ def test_tile_configs_host_side():
             sizes = [osw.os_tile_config_keys(kb, vb, c) for c in range(n_cfg)]
             assert all(t >= 256 for t in sizes)
             ws = osw.os_sort_workspace_bytes(osw.OS_KEY_U32 if kb == 32 else osw.OS_KEY_U64, 1_000_000, vb, 0, kb)
+            prev = osw.os_get_tile_config(kb, vb)
             for c in range(n_cfg):
                 assert osw.os_set_tile_config(kb, vb, c) == osw.OS_OK
                 assert osw.os_get_tile_config(kb, vb) == c
                 lay = osw.os_sort_workspace_layout(osw.OS_KEY_U32 if kb == 32 else osw.OS_KEY_U64, 1_000_000, vb, 0, kb)
                 assert lay.total_bytes == ws and lay.tile_keys == sizes[c]
-            osw.os_set_tile_config(kb, vb, 0)
+            osw.os_set_tile_config(kb, vb, prev)
     assert osw.os_set_tile_config(32, 0, n_cfg) == osw.OS_ERR_INVALID_ARG
     assert osw.os_set_tile_config(16, 0, 0) == osw.OS_ERR_INVALID_ARG
     assert osw.os_tile_config_keys(32, 3, 0) == 0
+
+
+def test_batch_workspace_and_validation():
+    u32 = osw.OS_KEY_U32
+    a = osw.os_sort_batch_workspace_bytes(u32, 1 << 20, 100, 4, 0, 32)
+    b = osw.os_sort_batch_workspace_bytes(u32, 1 << 20, 1000, 4, 0, 32)
+    assert 0 < a < b
+    assert osw.os_sort_batch_workspace_bytes(u32, 1 << 31, 10, 4, 0, 32) == 0
+    assert osw.os_sort_batch_workspace_bytes(u32, 100, -1, 4, 0, 32) == 0
+    assert osw.os_sort_batch_workspace_bytes(9, 100, 1, 4, 0, 32) == 0
+    fake = 1 << 40
+    ws = osw.os_sort_batch_workspace_bytes(u32, 1000, 4, 0, 0, 32)
+    # n_total == 0 or no segments: no-op before any CUDA call
+    assert osw.os_sort_batch(u32, None, None, None, None, None, 0, 0, 0, 32, None, 0, 0) == osw.OS_OK
+    # missing offsets, workspace too small, overlap
+    assert osw.os_sort_batch(u32, fake, fake + 8192, None, None, None, 4, 1000, 0, 32, fake + 65536, ws, 0) == \
+        osw.OS_ERR_INVALID_ARG
+    assert osw.os_sort_batch(u32, fake, fake + 8192, None, None, fake + 20000, 4, 1000, 0, 32, fake + 65536, ws - 1,
+                             0) == osw.OS_ERR_WORKSPACE
+    assert osw.os_sort_batch(u32, fake, fake + 400, None, None, fake + 20000, 4, 1000, 0, 32, fake + 65536, ws, 0) == \
+        osw.OS_ERR_INVALID_ARG

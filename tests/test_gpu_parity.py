@@ -267,6 +267,7 @@ def test_every_tile_config(cfg, kt):
     # every binning tile geometry gives the oracle's result (workspaces are
     # sized for the smallest tile, so the same sizing serves all of them)
     kb = KB[kt]
+    prev = {vb: osw.os_get_tile_config(kb, vb) for vb in (0, 4)}
     try:
         for pairs in (False, True):
             assert osw.os_set_tile_config(kb, 4 if pairs else 0, cfg) == osw.OS_OK
@@ -282,4 +283,4 @@ def test_every_tile_config(cfg, kt):
                     assert np.array_equal(got, exp), (cfg, n)
     finally:
         for vb in (0, 4):
-            osw.os_set_tile_config(kb, vb, 0)
+            osw.os_set_tile_config(kb, vb, prev[vb])
