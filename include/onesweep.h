@@ -71,7 +71,8 @@ typedef enum {
     OS_ERR_TOO_LARGE = 2,   /* n >= 2^30 */
     OS_ERR_WORKSPACE = 3,   /* workspace missing or smaller than required */
     OS_ERR_CUDA = 4,        /* a CUDA call or kernel launch failed */
-    OS_ERR_TIMEOUT = 5      /* a chained-scan look-back wait ran past its limit */
+    OS_ERR_TIMEOUT = 5,     /* a chained-scan look-back wait ran past its limit */
+    OS_ERR_SCRATCH_LIMIT = 6 /* os_sort_noalloc: the sort needs more than its fixed scratch */
 } os_status;
 
 /* Where the parts of a sort's workspace sit (byte offsets from ws). */
@@ -157,6 +158,41 @@ OS_API int os_workspace_status(const void *ws, void *stream);
 
 /* A static, human-readable name for an os_status value. */
 OS_API const char *os_status_string(int status);
+
+/*
+ * os_sort_noalloc - the same sort as os_sort_keys / os_sort_pairs for callers
+ * that cannot allocate device memory. The paper has no counterpart; this is a
+ * convenience of this library.
+ *
+ * Who needs it: code that runs where every byte of device memory already
+ * belongs to someone else's allocator (a host framework's memory pool with a
+ * hard budget, a plugin that must not allocate behind its host's back), or
+ * where a cudaMalloc/cudaFree would implicitly synchronize the device and
+ * stall a latency-critical pipeline. Such callers can pass their keys and
+ * values but cannot hand the sort a workspace.
+ *
+ * The scratch the sort needs (digit histograms, status counters, ping-pong
+ * buffers) lives in one fixed 16 MiB array of static device memory inside
+ * this library, so this call allocates nothing. Every GPU that loads the
+ * library holds those 16 MiB until the process exits. That bounds the
+ * problem size: a call whose workspace (os_sort_workspace_bytes) would exceed
+ * 16 MiB returns OS_ERR_SCRATCH_LIMIT and does nothing. Up to 2^20 keys always
+ * fit, for every key type, with or without values.
+ *
+ * Arguments as os_sort_pairs; vals_in and vals_out both NULL sorts keys only.
+ * The sort runs on the current device and `stream` must belong to it. The
+ * first call on a device looks up that device's copy of the scratch array
+ * (cudaGetSymbolAddress), so make that first call before any stream capture
+ * begins. All calls share the one array per device and each call leaves its
+ * contents behind (the sort re-initialises what it needs): calls that may
+ * overlap on the GPU (different streams without ordering between them) race
+ * on it and must be serialized by the caller. Device-side errors are reported
+ * by os_workspace_status() given the scratch address returned through
+ * `scratch_out` (may be NULL).
+ */
+OS_API int os_sort_noalloc(int key_type, const void *keys_in, void *keys_out, const uint32_t *vals_in,
+                           uint32_t *vals_out, uint64_t n, int begin_bit, int end_bit, void *stream,
+                           const void **scratch_out);
 
 /*
  * Tile geometry of the digit-binning kernel (tuning, not part of the method).

@@ -526,6 +526,14 @@ int run_batch(int key_type, const void* keys_in, void* keys_out, const uint32_t*
 }
 
 }  // namespace
+
+// The single-array sort on a workspace the caller already has (used by the
+// entry point that takes its scratch from static device memory).
+int sort_on_workspace(int key_type, const void* keys_in, void* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
+                      uint64_t n, int begin_bit, int end_bit, void* ws, size_t ws_bytes, void* stream) {
+  return run_sort(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws, ws_bytes, stream);
+}
+
 }  // namespace onesweep
 
 using namespace onesweep;
@@ -620,6 +628,7 @@ const char* os_status_string(int status) {
     case OS_ERR_WORKSPACE: return "workspace missing or too small";
     case OS_ERR_CUDA: return "CUDA error";
     case OS_ERR_TIMEOUT: return "chained-scan look-back wait ran past its limit";
+    case OS_ERR_SCRATCH_LIMIT: return "sort too large for the fixed 16 MiB scratch of os_sort_noalloc";
     default: return "unknown status";
   }
 }

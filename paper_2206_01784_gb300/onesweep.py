@@ -20,6 +20,7 @@ KEY_TYPES = {"u32": OS_KEY_U32, "u64": OS_KEY_U64, "f32": OS_KEY_F32, "f64": OS_
 KEY_BITS = {OS_KEY_U32: 32, OS_KEY_U64: 64, OS_KEY_F32: 32, OS_KEY_F64: 64}
 
 OS_OK, OS_ERR_INVALID_ARG, OS_ERR_TOO_LARGE, OS_ERR_WORKSPACE, OS_ERR_CUDA, OS_ERR_TIMEOUT = range(6)
+OS_ERR_SCRATCH_LIMIT = 6
 
 
 class OnesweepError(RuntimeError):
@@ -71,6 +72,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.os_sort_batch_workspace_bytes.argtypes = [i32, u64, i32, i32, i32, i32]
     lib.os_sort_batch.restype = i32
     lib.os_sort_batch.argtypes = [i32, vp, vp, vp, vp, vp, i32, u64, i32, i32, vp, sz, vp]
+    lib.os_sort_noalloc.restype = i32
+    lib.os_sort_noalloc.argtypes = [i32, vp, vp, vp, vp, u64, i32, i32, vp, ctypes.POINTER(ctypes.c_void_p)]
     lib.os_digit_histograms.restype = i32
     lib.os_digit_histograms.argtypes = [i32, vp, u64, i32, i32, vp, vp, vp, sz, vp]
     lib.os_workspace_status.restype = i32
@@ -128,6 +131,16 @@ def os_sort_batch(key_type, keys_in, keys_out, vals_in, vals_out, seg_offsets, n
                   end_bit, ws, ws_bytes, stream) -> int:
     return int(load().os_sort_batch(key_type, keys_in, keys_out, vals_in, vals_out, seg_offsets, num_segments,
                                     n_total, begin_bit, end_bit, ws, ws_bytes, stream))
+
+
+def os_sort_noalloc(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, stream):
+    """The sort for callers that cannot allocate device memory: its scratch is
+    a fixed 16 MiB of static device memory inside the library. Returns
+    (status, scratch device address for os_workspace_status)."""
+    scratch = ctypes.c_void_p(0)
+    rc = int(load().os_sort_noalloc(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, stream,
+                                    ctypes.byref(scratch)))
+    return rc, scratch.value
 
 
 def os_digit_histograms(key_type, keys_in, n, begin_bit, end_bit, hist_out, offsets_out, ws, ws_bytes,
