@@ -211,6 +211,18 @@ OS_API int os_set_tile_config(int key_bits, int value_bytes, int cfg);
 OS_API int os_get_tile_config(int key_bits, int value_bytes);
 
 /*
+ * The active geometry is kept per size bucket too (os_num_size_buckets()
+ * buckets; os_size_bucket(n) names the bucket of a sort of n keys, and a
+ * batch uses the bucket of its mean segment length). os_set_tile_config sets
+ * every bucket; these set or read one (os_get_tile_config reads the largest).
+ * Same return conventions as above.
+ */
+OS_API int os_num_size_buckets(void);
+OS_API int os_size_bucket(uint64_t n);
+OS_API int os_set_tile_config_bucket(int key_bits, int value_bytes, int bucket, int cfg);
+OS_API int os_get_tile_config_bucket(int key_bits, int value_bytes, int bucket);
+
+/*
  * Fault injection for tests of the look-back wait limit (not part of the
  * method). With tile >= 0, every later binning pass skips all status-counter
  * publishes of that tile, so the tiles after it wait until `spin_limit`

@@ -46,17 +46,25 @@ const BinningLaunch kBinningLaunch[2][2][2][4] = {
      {OS_BINNING_ROW(64, keys, seg), OS_BINNING_ROW(64, pairs, seg)}}};
 #undef OS_BINNING_ROW
 
-// Binning kernel variants: tile geometry (4) x digit-ranking method (2);
-// variant v uses geometry v % 4 and ranking v / 4 (0: one ballot per digit
-// bit, 1: shared-memory lane masks).
-constexpr int kGeometries = 4;
-constexpr int kTileConfigs = 2 * kGeometries;
+// Binning kernel variants: tile geometry (3) x digit-ranking method (3);
+// variant v uses geometry v % 3 and ranking v / 3 (0: one ballot per digit
+// bit, 1: shared-memory lane masks, 2: the two alternating by batch).
+constexpr int kGeometries = 3;
+constexpr int kTileConfigs = 3 * kGeometries;
 
-// Active variant per (key width, keys only / pairs); set by
-// os_set_tile_config (the autotuner's hook). Default: geometry 0 with
-// shared-memory lane masks (the fastest measured on GB300).
+// Active variant per (key width, keys only / pairs, size bucket); set by
+// os_set_tile_config / os_set_tile_config_bucket (the autotuner's hooks).
+// Default: geometry 0 with shared-memory lane masks (the fastest measured on
+// GB300 at 2^28 keys).
 constexpr int kDefaultTileConfig = kGeometries + 0;
-int g_tile_cfg[2][2] = {{kDefaultTileConfig, kDefaultTileConfig}, {kDefaultTileConfig, kDefaultTileConfig}};
+constexpr int kSizeBuckets = 4;  // n < 2^16, < 2^20, < 2^24, larger
+#define OS_FOUR_DEFAULTS {kDefaultTileConfig, kDefaultTileConfig, kDefaultTileConfig, kDefaultTileConfig}
+int g_tile_cfg[2][2][kSizeBuckets] = {{OS_FOUR_DEFAULTS, OS_FOUR_DEFAULTS}, {OS_FOUR_DEFAULTS, OS_FOUR_DEFAULTS}};
+#undef OS_FOUR_DEFAULTS
+
+int size_bucket(uint64_t n) { return n < (1u << 16) ? 0 : n < (1u << 20) ? 1 : n < (1u << 24) ? 2 : 3; }
+
+int& tile_cfg(int key_bits, bool pairs, int bucket) { return g_tile_cfg[key_bits == 64][pairs][bucket]; }
 
 uint32_t tile_keys_for(int key_bits, bool pairs, int cfg) {
   const int geo = cfg % kGeometries;
@@ -64,8 +72,8 @@ uint32_t tile_keys_for(int key_bits, bool pairs, int cfg) {
   return pairs ? binning_tile_keys64_pairs(geo) : binning_tile_keys64_keys(geo);
 }
 
-uint32_t binning_tile_keys(int key_bits, bool pairs) {
-  return tile_keys_for(key_bits, pairs, g_tile_cfg[key_bits == 64][pairs]);
+uint32_t binning_tile_keys(int key_bits, bool pairs, int bucket) {
+  return tile_keys_for(key_bits, pairs, tile_cfg(key_bits, pairs, bucket));
 }
 
 // Smallest tile over all geometries: workspaces are sized for it, so any
@@ -79,8 +87,8 @@ uint32_t min_tile_keys(int key_bits, bool pairs) {
   return t;
 }
 
-cudaError_t launch_binning(int key_bits, bool pairs, const PassArgs& a, cudaStream_t s) {
-  const int cfg = g_tile_cfg[key_bits == 64][pairs];
+cudaError_t launch_binning(int key_bits, bool pairs, int bucket, const PassArgs& a, cudaStream_t s) {
+  const int cfg = tile_cfg(key_bits, pairs, bucket);
   const int flip = (a.flip_in ? 1 : 0) | (a.flip_out ? 2 : 0);
   const int seg = a.seg_offsets != nullptr;
   return kBinningLaunch[seg][key_bits == 64][pairs][flip](cfg % kGeometries, cfg / kGeometries, a, s);
@@ -144,6 +152,7 @@ bool is_float(int key_type) { return key_type == OS_KEY_F32 || key_type == OS_KE
 struct Plan {
   int key_bits = 0;
   bool pairs = false;
+  int bucket = 0;
   int places = 0;
   uint32_t tile = 0;
   uint32_t tiles = 0;
@@ -159,7 +168,8 @@ int make_plan(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_
   plan->key_bits = kb;
   plan->pairs = value_bytes == 4;
   plan->places = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
-  plan->tile = binning_tile_keys(kb, plan->pairs);
+  plan->bucket = size_bucket(n);
+  plan->tile = binning_tile_keys(kb, plan->pairs, plan->bucket);
   plan->tiles = (uint32_t)((n + plan->tile - 1) / plan->tile);
   const uint32_t min_tile = min_tile_keys(kb, plan->pairs);
   const uint64_t max_tiles = (n + min_tile - 1) / min_tile;
@@ -320,7 +330,7 @@ int run_sort(int key_type, const void* keys_in, void* keys_out, const uint32_t* 
       return OS_ERR_INVALID_ARG;
     }
     const int slot = prof_begin(1, pass, s);
-    const cudaError_t e = launch_binning(plan.key_bits, pairs, a, s);
+    const cudaError_t e = launch_binning(plan.key_bits, pairs, plan.bucket, a, s);
     prof_end(slot, s);
     if (e != cudaSuccess) return OS_ERR_CUDA;
     src_k = dst_k;
@@ -343,6 +353,7 @@ constexpr size_t kTotalsWord = 2;
 struct BatchPlan {
   int key_bits = 0;
   bool pairs = false;
+  int bucket = 0;
   int places = 0;
   uint32_t tile = 0, small_max = 0;
   uint64_t max_tiles = 0, max_items = 0;
@@ -361,7 +372,8 @@ int make_batch_plan(int key_type, uint64_t n_total, int64_t num_segments, int va
   bp->key_bits = kb;
   bp->pairs = value_bytes == 4;
   bp->places = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
-  bp->tile = binning_tile_keys(kb, bp->pairs);
+  bp->bucket = size_bucket(S > 0 ? n_total / S : n_total);  // by the mean segment length
+  bp->tile = binning_tile_keys(kb, bp->pairs, bp->bucket);
   bp->small_max = batch_local_capacity(kb, bp->pairs);
   const uint32_t min_tile = min_tile_keys(kb, bp->pairs);
   bp->max_tiles = (n_total + min_tile - 1) / min_tile + S;
@@ -516,7 +528,7 @@ int run_batch(int key_type, const void* keys_in, void* keys_out, const uint32_t*
     a.tile_seg = b.tile_seg;
     a.total_tiles = b.totals;
     slot = prof_begin(1, pass, s);
-    e = launch_binning(bp.key_bits, pairs, a, s);
+    e = launch_binning(bp.key_bits, pairs, bp.bucket, a, s);
     prof_end(slot, s);
     if (e != cudaSuccess) return OS_ERR_CUDA;
     src_k = dst_k;
@@ -687,13 +699,32 @@ int os_set_tile_config(int key_bits, int value_bytes, int cfg) {
   if ((key_bits != 32 && key_bits != 64) || (value_bytes != 0 && value_bytes != 4) || cfg < 0 ||
       cfg >= kTileConfigs)
     return OS_ERR_INVALID_ARG;
-  g_tile_cfg[key_bits == 64][value_bytes == 4] = cfg;
+  for (int b = 0; b < kSizeBuckets; ++b) tile_cfg(key_bits, value_bytes == 4, b) = cfg;
   return OS_OK;
 }
 
 int os_get_tile_config(int key_bits, int value_bytes) {
   if ((key_bits != 32 && key_bits != 64) || (value_bytes != 0 && value_bytes != 4)) return -1;
-  return g_tile_cfg[key_bits == 64][value_bytes == 4];
+  return tile_cfg(key_bits, value_bytes == 4, kSizeBuckets - 1);
+}
+
+int os_num_size_buckets(void) { return kSizeBuckets; }
+
+int os_size_bucket(uint64_t n) { return size_bucket(n); }
+
+int os_set_tile_config_bucket(int key_bits, int value_bytes, int bucket, int cfg) {
+  if ((key_bits != 32 && key_bits != 64) || (value_bytes != 0 && value_bytes != 4) || cfg < 0 ||
+      cfg >= kTileConfigs || bucket < 0 || bucket >= kSizeBuckets)
+    return OS_ERR_INVALID_ARG;
+  tile_cfg(key_bits, value_bytes == 4, bucket) = cfg;
+  return OS_OK;
+}
+
+int os_get_tile_config_bucket(int key_bits, int value_bytes, int bucket) {
+  if ((key_bits != 32 && key_bits != 64) || (value_bytes != 0 && value_bytes != 4) || bucket < 0 ||
+      bucket >= kSizeBuckets)
+    return -1;
+  return tile_cfg(key_bits, value_bytes == 4, bucket);
 }
 
 void os_debug_set_lookback_fault(int64_t tile, uint32_t spin_limit) {

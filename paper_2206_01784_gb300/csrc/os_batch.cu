@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(LocalConfig<KBITS>::NT) batch_local_sort_kerne
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       const bool valid = wbase + i * 32 < len;
-      rank[i] = wlms_rank<kRankSmask, false>(wh, digit_of(key[i], shift, mask), valid, lane_bit);
+      rank[i] = wlms_rank<false>(wh, digit_of(key[i], shift, mask), valid, lane_bit, true);
     }
     __syncthreads();
     uint32_t total = 0;

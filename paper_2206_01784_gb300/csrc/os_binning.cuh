@@ -50,15 +50,15 @@ template <int KBITS, int CFG> struct TileShape;
 template <> struct TileShape<32, 0> { static constexpr int NT = 256, IPT = 24, MINB = 3; };
 template <> struct TileShape<32, 1> { static constexpr int NT = 256, IPT = 20, MINB = 3; };
 template <> struct TileShape<32, 2> { static constexpr int NT = 256, IPT = 16, MINB = 4; };
-template <> struct TileShape<32, 3> { static constexpr int NT = 512, IPT = 16, MINB = 2; };
 template <> struct TileShape<64, 0> { static constexpr int NT = 256, IPT = 12, MINB = 3; };
 template <> struct TileShape<64, 1> { static constexpr int NT = 256, IPT = 10, MINB = 3; };
 template <> struct TileShape<64, 2> { static constexpr int NT = 256, IPT = 8, MINB = 4; };
-template <> struct TileShape<64, 3> { static constexpr int NT = 512, IPT = 8, MINB = 2; };
+constexpr int kNumGeometries = 3;
 
 // Digit-ranking variants of step 4.
 constexpr int kRankBallot = 0;  // one ballot per digit bit (the paper's WLMS)
 constexpr int kRankSmask = 1;   // per-warp lane masks built with shared-memory atomic OR
+constexpr int kRankHybrid = 2;  // alternate the two by batch (spreads work over ALU and shared-memory pipes)
 
 template <int KBITS, bool PAIRS, int CFG = 0>
 struct BinningConfig {
@@ -115,10 +115,10 @@ struct TileCtx {
 
 // Warp-level multi-split ranking of one 32-key batch (step 4). Returns the
 // key's rank among the keys of the same digit in this warp's part of the tile.
-template <int RANK, bool FULL>
-__device__ __forceinline__ uint32_t wlms_rank(uint2* wh, uint32_t d, bool valid, uint32_t lane_bit) {
+template <bool FULL>
+__device__ __forceinline__ uint32_t wlms_rank(uint2* wh, uint32_t d, bool valid, uint32_t lane_bit, bool smask) {
   uint32_t peers, old;
-  if (RANK == kRankSmask) {
+  if (smask) {
     // every lane ORs its bit into its digit's mask word; OR commutes, so the
     // mask read back is exactly the lanes sharing the digit
     if (valid) atomicOr(&wh[d].x, lane_bit);
@@ -212,7 +212,8 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       const bool valid = FULL || wbase + i * 32 < count;
-      const uint32_t r = wlms_rank<RANK, FULL>(wh, digit_of(key[i], shift, mask), valid, lane_bit);
+      const bool smask = RANK == kRankSmask || (RANK == kRankHybrid && (i & 1));
+      const uint32_t r = wlms_rank<FULL>(wh, digit_of(key[i], shift, mask), valid, lane_bit, smask);
       if (i & 1)
         rank2[i / 2] |= r << 16;
       else
@@ -458,7 +459,6 @@ cudaError_t launch_binning_flip_rank(const PassArgs& a, cudaStream_t s, int cfg)
   switch (cfg) {
     case 1: return launch_binning_one<KBITS, PAIRS, 1, RANK, FLIP, SEG>(a, s);
     case 2: return launch_binning_one<KBITS, PAIRS, 2, RANK, FLIP, SEG>(a, s);
-    case 3: return launch_binning_one<KBITS, PAIRS, 3, RANK, FLIP, SEG>(a, s);
     default: return launch_binning_one<KBITS, PAIRS, 0, RANK, FLIP, SEG>(a, s);
   }
 }
@@ -468,8 +468,11 @@ cudaError_t launch_binning_flip_rank(const PassArgs& a, cudaStream_t s, int cfg)
 // blocks (an upper bound in segmented mode; blocks beyond the last tile exit).
 template <int KBITS, bool PAIRS, int FLIP, bool SEG>
 cudaError_t launch_binning_flip(const PassArgs& a, cudaStream_t s, int cfg, int rank) {
-  return rank == kRankSmask ? launch_binning_flip_rank<KBITS, PAIRS, FLIP, kRankSmask, SEG>(a, s, cfg)
-                            : launch_binning_flip_rank<KBITS, PAIRS, FLIP, kRankBallot, SEG>(a, s, cfg);
+  switch (rank) {
+    case kRankSmask: return launch_binning_flip_rank<KBITS, PAIRS, FLIP, kRankSmask, SEG>(a, s, cfg);
+    case kRankHybrid: return launch_binning_flip_rank<KBITS, PAIRS, FLIP, kRankHybrid, SEG>(a, s, cfg);
+    default: return launch_binning_flip_rank<KBITS, PAIRS, FLIP, kRankBallot, SEG>(a, s, cfg);
+  }
 }
 
 template <int KBITS, bool PAIRS>
@@ -477,7 +480,6 @@ uint32_t tile_keys_t(int cfg) {
   switch (cfg) {
     case 1: return BinningConfig<KBITS, PAIRS, 1>::T;
     case 2: return BinningConfig<KBITS, PAIRS, 2>::T;
-    case 3: return BinningConfig<KBITS, PAIRS, 3>::T;
     default: return BinningConfig<KBITS, PAIRS, 0>::T;
   }
 }

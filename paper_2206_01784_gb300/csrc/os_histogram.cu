@@ -1,17 +1,21 @@
 // Phase 1 and 2 of Onesweep (arXiv 2206.01784, Section 3, "Upfront histogram
 // kernel" and "Exclusive sum kernel"; Figure 5).
 //
-// A grid sized to the SM count walks the keys tile-cyclically with 128-bit
-// streaming loads. Each block keeps private per-place digit histograms in
-// shared memory, updated by shared-memory atomics, and adds them to the
-// global histograms with global atomics when done. The block that finishes
-// last then takes the exclusive prefix sum of every place's histogram,
-// producing the global bin offsets: the paper's separate exclusive-sum kernel
-// is folded into the histogram kernel's last block (one launch fewer).
+// A grid of one block per SM walks the keys tile-cyclically with 128-bit
+// streaming loads and counts the digits of every place with shared-memory
+// atomics into block-private histograms, which are added to the global
+// histograms with global atomics at the end (the paper's scheme). The block
+// that finishes last then takes the exclusive prefix sum of every place's
+// histogram - the global bin offsets - so the paper's separate exclusive-sum
+// kernel is folded into the histogram kernel's last block (one launch fewer).
 //
-// Skewed keys (low-entropy bands, all-equal keys) make many lanes hit one
-// shared counter. Each thread therefore first merges runs of equal digits
-// among its own keys and issues one atomic per run.
+// GB300 layout of the block-private histograms: each lane of a warp owns its
+// own copy, interleaved so that lane l's counters all sit in shared-memory bank
+// l (counter e of copy c at word e * kCopies + c). Every atomic of a warp then
+// touches 32 distinct banks (one wavefront), and lanes never contend for one
+// address, so skewed key distributions (low-entropy bands, all-equal keys) cost
+// the same as uniform ones. 32-bit keys (4 places) keep 32 copies; 64-bit keys
+// (8 places) keep 16 (two lanes per copy), both 128 KiB per block.
 //
 // On the way, the grid also zeroes the status-counter slab of the first
 // binning pass, so no separate memset of it is needed.
@@ -22,9 +26,16 @@ namespace onesweep {
 
 namespace {
 
-constexpr int kHistThreads = 512;
-constexpr int kHistVec = 4;          // 16-byte loads in flight per thread per step
-constexpr int kHistBlocksPerSm = 2;
+constexpr int kHistThreads = 1024;
+constexpr int kHistVec = 4;  // 16-byte loads in flight per thread per step
+
+template <int KBITS>
+struct HistLayout {
+  static constexpr int P = KBITS / 8;              // most places a key can have
+  static constexpr int kCopies = KBITS == 32 ? 32 : 16;
+  static constexpr int kEntries = P * kRadix;
+  static constexpr size_t smem_bytes = (size_t)kEntries * kCopies * 4;
+};
 
 template <int KBITS>
 __device__ __forceinline__ void unpack(const uint4& v, typename KeyWord<KBITS>::type* out);
@@ -39,18 +50,22 @@ __device__ __forceinline__ void unpack<64>(const uint4& v, uint64_t* out) {
 }
 
 template <int KBITS>
-__global__ void __launch_bounds__(kHistThreads, kHistBlocksPerSm) histogram_kernel(HistArgs a) {
+__global__ void __launch_bounds__(kHistThreads, 1) histogram_kernel(HistArgs a) {
   using K = typename KeyWord<KBITS>::type;
-  constexpr int P = KBITS / 8;                // most places a key can have
-  constexpr int PER_VEC = 128 / KBITS;        // keys per 16-byte vector
-  constexpr int KPT = kHistVec * PER_VEC;     // keys per thread per step
-  __shared__ uint32_t sh[P * kRadix];
+  using L = HistLayout<KBITS>;
+  constexpr int P = L::P, C = L::kCopies;
+  constexpr int PER_VEC = 128 / KBITS;     // keys per 16-byte vector
+  constexpr int KPT = kHistVec * PER_VEC;  // keys per thread per step
+  extern __shared__ __align__(16) uint32_t sh[];  // [P * 256][kCopies]
   __shared__ uint32_t scan_tmp[kHistThreads / 32 + 1];
   __shared__ uint32_t s_last;
 
   const int tid = threadIdx.x;
   const int p = a.num_places;
-  for (int i = tid; i < P * kRadix; i += kHistThreads) sh[i] = 0;
+  {
+    uint4* s4 = reinterpret_cast<uint4*>(sh);
+    for (int i = tid; i < L::kEntries * C / 4; i += kHistThreads) s4[i] = make_uint4(0, 0, 0, 0);
+  }
 
   // zero the first pass's status slab (grid-stride, 16-byte stores)
   if (a.clear) {
@@ -62,8 +77,18 @@ __global__ void __launch_bounds__(kHistThreads, kHistBlocksPerSm) histogram_kern
   __syncthreads();
 
   const uint32_t last_mask = (1u << (a.end_bit - (a.begin_bit + 8 * (p - 1)))) - 1u;
-  auto place_mask = [&](int pl) -> uint32_t { return pl == p - 1 ? last_mask : 0xFFu; };
-  auto ordered = [&](K k) -> K { return a.flip ? flip_to_ordered(k) : k; };
+  // this lane's copy: counter (place, digit) at word ((place * 256 + digit) * C + copy)
+  uint32_t* mine = sh + (tid & 31) % C;
+  auto count_key = [&](K k) {
+    const K o = a.flip ? flip_to_ordered(k) : k;
+#pragma unroll
+    for (int pl = 0; pl < P; ++pl) {
+      if (pl < p) {
+        const uint32_t d = digit_of(o, a.begin_bit + 8 * pl, pl == p - 1 ? last_mask : 0xFFu);
+        atomicAdd(mine + (pl * kRadix + d) * C, 1u);
+      }
+    }
+  };
 
   const K* keys = static_cast<const K*>(a.keys);
   const uintptr_t addr = reinterpret_cast<uintptr_t>(keys);
@@ -75,47 +100,22 @@ __global__ void __launch_bounds__(kHistThreads, kHistBlocksPerSm) histogram_kern
 
   const uint64_t step = (uint64_t)gridDim.x * kHistThreads * kHistVec;
   for (uint64_t base = (uint64_t)blockIdx.x * kHistThreads * kHistVec; base < nvec; base += step) {
-    K k[KPT];
     if (base + (uint64_t)kHistThreads * kHistVec <= nvec) {
       uint4 v[kHistVec];
 #pragma unroll
       for (int u = 0; u < kHistVec; ++u) v[u] = __ldcs(vkeys + base + (uint64_t)u * kHistThreads + tid);
+      K k[KPT];
 #pragma unroll
       for (int u = 0; u < kHistVec; ++u) unpack<KBITS>(v[u], k + u * PER_VEC);
 #pragma unroll
-      for (int j = 0; j < KPT; ++j) k[j] = ordered(k[j]);
-#pragma unroll
-      for (int pl = 0; pl < P; ++pl) {
-        if (pl < p) {
-          const int shift = a.begin_bit + 8 * pl;
-          const uint32_t mask = place_mask(pl);
-          uint32_t* h = sh + pl * kRadix;
-          uint32_t run_digit = digit_of(k[0], shift, mask), run_len = 1;
-#pragma unroll
-          for (int j = 1; j < KPT; ++j) {
-            uint32_t d = digit_of(k[j], shift, mask);
-            if (d == run_digit) {
-              ++run_len;
-            } else {
-              atomicAdd(h + run_digit, run_len);
-              run_digit = d;
-              run_len = 1;
-            }
-          }
-          atomicAdd(h + run_digit, run_len);
-        }
-      }
+      for (int j = 0; j < KPT; ++j) count_key(k[j]);
     } else {
-      // last, partial step: one key at a time
       for (int u = 0; u < kHistVec; ++u) {
         const uint64_t idx = base + (uint64_t)u * kHistThreads + tid;
         if (idx < nvec) {
           K kk[PER_VEC];
           unpack<KBITS>(__ldcs(vkeys + idx), kk);
-          for (int j = 0; j < PER_VEC; ++j) {
-            const K o = ordered(kk[j]);
-            for (int pl = 0; pl < p; ++pl) atomicAdd(sh + pl * kRadix + digit_of(o, a.begin_bit + 8 * pl, place_mask(pl)), 1u);
-          }
+          for (int j = 0; j < PER_VEC; ++j) count_key(kk[j]);
         }
       }
     }
@@ -125,15 +125,19 @@ __global__ void __launch_bounds__(kHistThreads, kHistBlocksPerSm) histogram_kern
     const uint64_t extra = head + (a.n - tail_start);
     if ((uint64_t)tid < extra) {
       const uint64_t i = (uint64_t)tid < head ? (uint64_t)tid : tail_start + (tid - head);
-      const K o = ordered(keys[i]);
-      for (int pl = 0; pl < p; ++pl) atomicAdd(sh + pl * kRadix + digit_of(o, a.begin_bit + 8 * pl, place_mask(pl)), 1u);
+      count_key(keys[i]);
     }
   }
   __syncthreads();
 
-  for (int i = tid; i < p * kRadix; i += kHistThreads) {
-    const uint32_t c = sh[i];
-    if (c) atomicAdd(a.hist + i, c);
+  // add the block's copies of every counter (each lane starts at a different
+  // copy, so a warp's reads hit distinct banks) and flush to global memory
+  const int lane = tid & 31;
+  for (int e = tid; e < p * kRadix; e += kHistThreads) {
+    uint32_t sum = 0;
+#pragma unroll 8
+    for (int c = 0; c < C; ++c) sum += sh[e * C + ((c + lane) % C)];
+    if (sum) atomicAdd(a.hist + e, sum);
   }
 
   // Phase 2 in the last block to finish: exclusive sum of each place's counts.
@@ -151,6 +155,21 @@ __global__ void __launch_bounds__(kHistThreads, kHistBlocksPerSm) histogram_kern
   }
 }
 
+template <int KBITS>
+cudaError_t launch_hist_t(const HistArgs& a, int grid, cudaStream_t s) {
+  constexpr size_t bytes = HistLayout<KBITS>::smem_bytes;
+  static int configured_device = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_device != dev) {
+    cudaError_t e = cudaFuncSetAttribute(histogram_kernel<KBITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    configured_device = dev;
+  }
+  histogram_kernel<KBITS><<<grid, kHistThreads, bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_histogram(int key_bits, const HistArgs& a, int num_sms, cudaStream_t s) {
@@ -158,17 +177,12 @@ cudaError_t launch_histogram(int key_bits, const HistArgs& a, int num_sms, cudaS
   const uint64_t nvec = a.n / per_vec + 1;
   const uint64_t per_block = (uint64_t)kHistThreads * kHistVec;
   uint64_t want = (nvec + per_block - 1) / per_block;
-  uint64_t cap = (uint64_t)num_sms * kHistBlocksPerSm;
-  // enough blocks to also zero the status slab quickly
+  const uint64_t cap = (uint64_t)num_sms;  // one 1024-thread block per SM (128 KiB of shared memory)
   const uint64_t clear_blocks = (a.clear_words / 4 + kHistThreads - 1) / kHistThreads;
   if (want < clear_blocks) want = clear_blocks;
   int grid = (int)(want < cap ? want : cap);
   if (grid < 1) grid = 1;
-  if (key_bits == 32)
-    histogram_kernel<32><<<grid, kHistThreads, 0, s>>>(a);
-  else
-    histogram_kernel<64><<<grid, kHistThreads, 0, s>>>(a);
-  return cudaGetLastError();
+  return key_bits == 32 ? launch_hist_t<32>(a, grid, s) : launch_hist_t<64>(a, grid, s);
 }
 
 }  // namespace onesweep

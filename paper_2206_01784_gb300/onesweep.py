@@ -90,6 +90,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.os_set_tile_config.argtypes = [i32, i32, i32]
     lib.os_get_tile_config.restype = i32
     lib.os_get_tile_config.argtypes = [i32, i32]
+    lib.os_num_size_buckets.restype = i32
+    lib.os_num_size_buckets.argtypes = []
+    lib.os_size_bucket.restype = i32
+    lib.os_size_bucket.argtypes = [u64]
+    lib.os_set_tile_config_bucket.restype = i32
+    lib.os_set_tile_config_bucket.argtypes = [i32, i32, i32, i32]
+    lib.os_get_tile_config_bucket.restype = i32
+    lib.os_get_tile_config_bucket.argtypes = [i32, i32, i32]
     lib.os_profile_start.restype = i32
     lib.os_profile_start.argtypes = [i32]
     lib.os_profile_stop.restype = i32
@@ -178,6 +186,22 @@ def os_set_tile_config(key_bits: int, value_bytes: int, cfg: int) -> int:
 
 def os_get_tile_config(key_bits: int, value_bytes: int) -> int:
     return int(load().os_get_tile_config(key_bits, value_bytes))
+
+
+def os_num_size_buckets() -> int:
+    return int(load().os_num_size_buckets())
+
+
+def os_size_bucket(n: int) -> int:
+    return int(load().os_size_bucket(n))
+
+
+def os_set_tile_config_bucket(key_bits: int, value_bytes: int, bucket: int, cfg: int) -> int:
+    return int(load().os_set_tile_config_bucket(key_bits, value_bytes, bucket, cfg))
+
+
+def os_get_tile_config_bucket(key_bits: int, value_bytes: int, bucket: int) -> int:
+    return int(load().os_get_tile_config_bucket(key_bits, value_bytes, bucket))
 
 
 def os_profile_start(capacity: int) -> int:

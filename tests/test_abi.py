@@ -137,3 +137,29 @@ def test_batch_workspace_and_validation():
                              0) == osw.OS_ERR_WORKSPACE
     assert osw.os_sort_batch(u32, fake, fake + 400, None, None, fake + 20000, 4, 1000, 0, 32, fake + 65536, ws, 0) == \
         osw.OS_ERR_INVALID_ARG
+
+
+def test_size_buckets_and_tuning_table_roundtrip(tmp_path):
+    from paper_2206_01784_gb300 import autotune
+
+    nb = osw.os_num_size_buckets()
+    assert nb == 4
+    assert [osw.os_size_bucket(n) for n in (1, 65535, 65536, (1 << 20) - 1, 1 << 20, 1 << 24, 1 << 29)] == \
+        [0, 0, 1, 1, 2, 3, 3]
+    saved = autotune.current()
+    try:
+        table = {(32, 4, 1): {"cfg": 2}, (64, 0, 3): {"cfg": 5}}
+        autotune.apply(table)
+        assert osw.os_get_tile_config_bucket(32, 4, 1) == 2
+        assert osw.os_get_tile_config_bucket(64, 0, 3) == 5
+        assert osw.os_get_tile_config(64, 0) == 5  # the largest bucket
+        # the tile of a sort follows its size bucket
+        lay = osw.os_sort_workspace_layout(osw.OS_KEY_U32, 100_000, 4, 0, 32)
+        assert lay.tile_keys == osw.os_tile_config_keys(32, 4, 2)
+        p = tmp_path / "tiles.json"
+        autotune.save(table, str(p), "test")
+        assert autotune.load(str(p)) == table
+        assert osw.os_set_tile_config_bucket(32, 4, nb, 0) == osw.OS_ERR_INVALID_ARG
+        assert osw.os_get_tile_config_bucket(32, 4, -1) == -1
+    finally:
+        autotune.apply(saved)

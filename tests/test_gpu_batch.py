@@ -172,7 +172,7 @@ def test_batch_cuda_graph_replay():
         assert np.array_equal(vo.cpu().numpy().view(np.uint32), ev)
 
 
-@pytest.mark.parametrize("cfg", list(range(8)))
+@pytest.mark.parametrize("cfg", list(range(9)))
 def test_batch_every_tile_config(cfg):
     prev = osw.os_get_tile_config(32, 4)
     try:

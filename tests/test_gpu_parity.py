@@ -261,7 +261,7 @@ def test_lookback_wait_limit_reports_timeout():
     assert np.array_equal(to_host(out, np.uint32), oracle.sort("u32", keys))
 
 
-@pytest.mark.parametrize("cfg", list(range(8)))
+@pytest.mark.parametrize("cfg", list(range(9)))
 @pytest.mark.parametrize("kt", ["u32", "u64", "f32"])
 def test_every_tile_config(cfg, kt):
     # every binning tile geometry gives the oracle's result (workspaces are
@@ -284,3 +284,24 @@ def test_every_tile_config(cfg, kt):
     finally:
         for vb in (0, 4):
             osw.os_set_tile_config(kb, vb, prev[vb])
+
+
+def test_autotune_small_buckets_keeps_results():
+    from paper_2206_01784_gb300 import autotune
+
+    _dev()
+    saved = autotune.current()
+    try:
+        table = autotune.tune(key_bits=(32,), value_bytes=(4,), buckets=(0, 1), steps=2, warmup=1)
+        for b in (0, 1):
+            rec = table[(32, 4, b)]
+            assert len(rec["ms"]) == osw.os_num_tile_configs() and all(t > 0 for t in rec["ms"])
+            assert osw.os_get_tile_config_bucket(32, 4, b) == rec["cfg"]
+        n = 300_007
+        keys = make_keys("u32", "and2", n, seed=99)
+        vals = workload.iota_u32(n)
+        got = gpu_sort("u32", keys, vals)
+        exp = oracle.sort("u32", keys, vals)
+        assert np.array_equal(got[0], exp[0]) and np.array_equal(got[1], exp[1])
+    finally:
+        autotune.apply(saved)
