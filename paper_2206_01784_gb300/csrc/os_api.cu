@@ -48,14 +48,15 @@ const BinningLaunch kBinningLaunch[2][2][2][4] = {
 
 // Binning kernel variants: tile geometry (3) x digit-ranking method (3);
 // variant v uses geometry v % 3 and ranking v / 3 (0: one ballot per digit
-// bit, 1: shared-memory lane masks, 2: the two alternating by batch).
+// bit; 1: adaptive - ballots where the place is skewed, else the hybrid;
+// 2: hybrid - ballots and shared-memory lane masks alternating by batch).
 constexpr int kGeometries = 3;
 constexpr int kTileConfigs = 3 * kGeometries;
 
 // Active variant per (key width, keys only / pairs, size bucket); set by
 // os_set_tile_config / os_set_tile_config_bucket (the autotuner's hooks).
-// Default: geometry 0 with shared-memory lane masks (the fastest measured on
-// GB300 at 2^28 keys).
+// Default: geometry 0 with adaptive ranking (the fastest measured on GB300 at
+// 2^28 keys across the key distributions).
 constexpr int kDefaultTileConfig = kGeometries + 0;
 constexpr int kSizeBuckets = 4;  // n < 2^16, < 2^20, < 2^24, larger
 #define OS_FOUR_DEFAULTS {kDefaultTileConfig, kDefaultTileConfig, kDefaultTileConfig, kDefaultTileConfig}
@@ -105,6 +106,7 @@ constexpr uint32_t kDefaultSpinLimit = 1u << 22;
 constexpr size_t kHeaderBytes = 256;
 constexpr size_t kDoneWord = 1;
 constexpr size_t kTileCounterWord = 16;
+constexpr size_t kSkewWord = 32;  // 8 skewed-place flags of a single sort
 
 int64_t g_fault_tile = -1;
 uint32_t g_spin_limit = kDefaultSpinLimit;
@@ -231,6 +233,7 @@ int run_histogram(const Plan& plan, int key_type, const void* keys, uint64_t n, 
   h.done_counter = reinterpret_cast<uint32_t*>(ws) + kDoneWord;
   h.clear = clear_slab0 ? reinterpret_cast<uint32_t*>(ws + plan.layout.status_offset[0]) : nullptr;
   h.clear_words = clear_slab0 ? (uint64_t)plan.tiles * kRadix : 0;
+  h.skew = reinterpret_cast<uint32_t*>(ws) + kSkewWord;
   const int sms = device_sm_count();
   if (sms <= 0) return OS_ERR_CUDA;
   const int slot = prof_begin(0, -1, s);
@@ -325,6 +328,7 @@ int run_sort(int key_type, const void* keys_in, void* keys_out, const uint32_t* 
     a.error = header;
     a.spin_limit = g_spin_limit;
     a.fault_tile = g_fault_tile;
+    a.skew_flags = header + kSkewWord + pass;
     if (pass >= 8) {
       // more than 8 passes cannot happen with 8-bit digits of <= 64-bit keys
       return OS_ERR_INVALID_ARG;
@@ -357,7 +361,7 @@ struct BatchPlan {
   int places = 0;
   uint32_t tile = 0, small_max = 0;
   uint64_t max_tiles = 0, max_items = 0;
-  size_t seg_done = 0, seg_hist = 0, zero_end = 0, seg_bin_offsets = 0, tile_base = 0, hist_base = 0;
+  size_t seg_done = 0, seg_skew = 0, seg_hist = 0, zero_end = 0, seg_bin_offsets = 0, tile_base = 0, hist_base = 0;
   size_t tile_seg = 0, hist_seg = 0, status[2] = {0, 0}, alt_keys = 0, alt_vals = 0, total = 0;
 };
 
@@ -382,6 +386,8 @@ int make_batch_plan(int key_type, uint64_t n_total, int64_t num_segments, int va
   size_t off = kHeaderBytes;
   bp->seg_done = off;
   off = round_up(off + S * 4);
+  bp->seg_skew = off;
+  off = round_up(off + S * (size_t)(bp->places > 0 ? bp->places : 1) * 4);
   bp->seg_hist = off;
   off = round_up(off + S * per_seg);
   bp->zero_end = off;
@@ -476,6 +482,7 @@ int run_batch(int key_type, const void* keys_in, void* keys_out, const uint32_t*
   b.seg_done = reinterpret_cast<uint32_t*>(w + bp.seg_done);
   b.seg_hist = reinterpret_cast<uint32_t*>(w + bp.seg_hist);
   b.seg_bin_offsets = reinterpret_cast<uint32_t*>(w + bp.seg_bin_offsets);
+  b.seg_skew = reinterpret_cast<uint32_t*>(w + bp.seg_skew);
   b.error = header;
   b.clear = reinterpret_cast<uint32_t*>(w + bp.status[0]);
   b.clear_words = bp.max_tiles * kRadix;
@@ -527,6 +534,8 @@ int run_batch(int key_type, const void* keys_in, void* keys_out, const uint32_t*
     a.tile_base = b.tile_base;
     a.tile_seg = b.tile_seg;
     a.total_tiles = b.totals;
+    a.skew_flags = b.seg_skew + pass;
+    a.skew_stride = (uint32_t)bp.places;
     slot = prof_begin(1, pass, s);
     e = launch_binning(bp.key_bits, pairs, bp.bucket, a, s);
     prof_end(slot, s);

@@ -55,10 +55,15 @@ template <> struct TileShape<64, 1> { static constexpr int NT = 256, IPT = 10, M
 template <> struct TileShape<64, 2> { static constexpr int NT = 256, IPT = 8, MINB = 4; };
 constexpr int kNumGeometries = 3;
 
-// Digit-ranking variants of step 4.
-constexpr int kRankBallot = 0;  // one ballot per digit bit (the paper's WLMS)
-constexpr int kRankSmask = 1;   // per-warp lane masks built with shared-memory atomic OR
-constexpr int kRankHybrid = 2;  // alternate the two by batch (spreads work over ALU and shared-memory pipes)
+// Digit-ranking variants of step 4. Two methods find the lanes sharing a
+// digit: ballots (one per digit bit, the paper's WLMS; ALU work, insensitive
+// to the key distribution) and shared-memory lane masks (every lane ORs its
+// bit into its digit's mask word; shared-memory work that slows down when
+// many lanes share a digit).
+constexpr int kRankBallot = 0;    // ballots only
+constexpr int kRankAdaptive = 1;  // hybrid, or ballots only where the pass's place is skewed
+constexpr int kRankHybrid = 2;    // alternate the two methods by batch (spreads the work over
+                                  // the ALU and shared-memory pipes)
 
 template <int KBITS, bool PAIRS, int CFG = 0>
 struct BinningConfig {
@@ -110,6 +115,7 @@ struct TileCtx {
   uint32_t out_base;     // array index of the chain's (segment's) first key
   uint32_t out_len;      // keys in the chain's segment
   uint32_t bulk;         // staged by bulk copies (wait on the mbarriers)
+  uint32_t skewed;       // this place (of this segment) is skewed: rank with ballots only
   const uint32_t* bin_offsets;  // this place's 256 bin offsets (segment-relative)
 };
 
@@ -212,7 +218,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       const bool valid = FULL || wbase + i * 32 < count;
-      const bool smask = RANK == kRankSmask || (RANK == kRankHybrid && (i & 1));
+      const bool smask = (RANK == kRankHybrid || (RANK == kRankAdaptive && !c.skewed)) && (i & 1);
       const uint32_t r = wlms_rank<FULL>(wh, digit_of(key[i], shift, mask), valid, lane_bit, smask);
       if (i & 1)
         rank2[i / 2] |= r << 16;
@@ -382,6 +388,7 @@ __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS, CFG>::NT, BinningC
           c.out_base = (uint32_t)s0;
           c.out_len = len;
           c.bin_offsets = a.bin_offsets + (size_t)seg * a.offsets_stride;
+        if (RANK == kRankAdaptive && a.skew_flags) c.skewed = a.skew_flags[(size_t)seg * a.skew_stride];
         }
       }
     } else if (tile < a.num_tiles) {
@@ -391,6 +398,7 @@ __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS, CFG>::NT, BinningC
       c.out_base = 0;
       c.out_len = a.n;
       c.bin_offsets = a.bin_offsets;
+      if (RANK == kRankAdaptive && a.skew_flags) c.skewed = a.skew_flags[0];
     }
     if (c.count > 0 && a.use_bulk) {
       // the 16-byte-aligned span covering the tile, if it stays in the array
@@ -469,7 +477,7 @@ cudaError_t launch_binning_flip_rank(const PassArgs& a, cudaStream_t s, int cfg)
 template <int KBITS, bool PAIRS, int FLIP, bool SEG>
 cudaError_t launch_binning_flip(const PassArgs& a, cudaStream_t s, int cfg, int rank) {
   switch (rank) {
-    case kRankSmask: return launch_binning_flip_rank<KBITS, PAIRS, FLIP, kRankSmask, SEG>(a, s, cfg);
+    case kRankAdaptive: return launch_binning_flip_rank<KBITS, PAIRS, FLIP, kRankAdaptive, SEG>(a, s, cfg);
     case kRankHybrid: return launch_binning_flip_rank<KBITS, PAIRS, FLIP, kRankHybrid, SEG>(a, s, cfg);
     default: return launch_binning_flip_rank<KBITS, PAIRS, FLIP, kRankBallot, SEG>(a, s, cfg);
   }

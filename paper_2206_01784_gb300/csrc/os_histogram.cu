@@ -151,7 +151,11 @@ __global__ void __launch_bounds__(kHistThreads, 1) histogram_kernel(HistArgs a) 
     const uint32_t c = tid < kRadix ? ld_relaxed_gpu(a.hist + pl * kRadix + tid) : 0u;
     const uint32_t excl = block_exclusive_sum<kHistThreads>(c, scan_tmp);
     if (tid < kRadix) a.offsets[pl * kRadix + tid] = excl;
-    __syncthreads();
+    // a place where one digit holds over 1/16 of the keys is "skewed": its
+    // binning pass ranks with ballots, which do not slow down when many lanes
+    // share a digit
+    const int skewed = __syncthreads_or(tid < kRadix && (uint64_t)c * 16u > a.n);
+    if (tid == 0 && a.skew) a.skew[pl] = skewed ? 1u : 0u;
   }
 }
 

@@ -21,6 +21,7 @@ struct HistArgs {
   uint32_t* done_counter;    // zeroed by the caller (device)
   uint32_t* clear;           // words to zero on the way (status slab of pass 0), may be null
   uint64_t clear_words;
+  uint32_t* skew;            // [p] set to 1 where one digit holds over 1/16 of the keys (may be null)
 };
 
 // Phase 3, one digit-binning pass (Section 3, "Chained scan digit-binning kernel").
@@ -52,6 +53,11 @@ struct PassArgs {
   const uint32_t* tile_seg;      // [tiles] segment of each tile
   const uint32_t* total_tiles;   // device word: tiles in this pass
   uint32_t offsets_stride;       // words between two segments' bin offsets
+
+  // Skewed-place flags from the histogram pass (null: none); the flag of
+  // segment s (0 for one array) is skew_flags[s * skew_stride].
+  const uint32_t* skew_flags;
+  uint32_t skew_stride;
 };
 
 // Segmented sort: the plan, per-segment histograms and the one-block sort of
@@ -81,6 +87,7 @@ struct BatchArgs {
   uint32_t* seg_done;            // [S] zeroed
   uint32_t* seg_hist;            // [S][p][256] zeroed
   uint32_t* seg_bin_offsets;     // [S][p][256]
+  uint32_t* seg_skew;            // [S][p] skewed-place flags
   uint32_t* error;
   uint32_t* clear;               // status slab of the first pass, to zero
   uint64_t clear_words;
