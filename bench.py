@@ -47,6 +47,8 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--keys-only", action="store_true", help="sort keys without values")
+    p.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
+    p.add_argument("--serve-requests", type=int, default=10000)
     return p.parse_args()
 
 
@@ -205,6 +207,95 @@ def run_reference(args):
     return 0
 
 
+def measure_batch(torch, osw, workload, np, dev, steps: int = 20):
+    """4096 lognormal segments (median 32K keys, clipped 1K-4M, seed 10) of u32
+    keys + u32 values: one graph-captured os_sort_batch against one
+    os_sort_pairs call per segment on one stream; outputs must be identical."""
+    sizes = workload.segment_sizes(4096, seed=10)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(offs[-1])
+    keys = workload.keys("u32", "uniform", n, 10)
+    k = torch.from_numpy(keys.view(np.int32)).to(dev)
+    v = torch.from_numpy(workload.iota_u32(n).view(np.int32)).to(dev)
+    o = torch.from_numpy(offs).to(dev)
+    bk, bv = torch.empty_like(k), torch.empty_like(v)
+    ws = osw.batch_workspace(osw.OS_KEY_U32, n, len(sizes), 4, 0, 32, dev)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        osw.sort_batch(k, o, v, key_type="u32", keys_out=bk, values_out=bv, ws=ws)  # warm-up before capture
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        osw.sort_batch(k, o, v, key_type="u32", keys_out=bk, values_out=bv, ws=ws)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    t_batch = e0.elapsed_time(e1) / steps
+    pk, pv = torch.empty_like(k), torch.empty_like(v)
+    wss = osw.workspace(osw.OS_KEY_U32, int(sizes.max()), 4, 0, 32, dev)
+    sp = torch.cuda.current_stream(dev).cuda_stream
+
+    def per_array():
+        for i in range(len(sizes)):
+            lo, hi = int(offs[i]), int(offs[i + 1])
+            rc = osw.os_sort_pairs(osw.OS_KEY_U32, k.data_ptr() + 4 * lo, pk.data_ptr() + 4 * lo,
+                                   v.data_ptr() + 4 * lo, pv.data_ptr() + 4 * lo, hi - lo, 0, 32, wss.data_ptr(),
+                                   wss.numel(), sp)
+            if rc != osw.OS_OK:
+                raise osw.OnesweepError(rc, "os_sort_pairs")
+
+    per_array()
+    torch.cuda.synchronize(dev)
+    e0.record()
+    per_array()
+    per_array()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    t_per = e0.elapsed_time(e1) / 2
+    identical = bool(torch.equal(bk, pk) and torch.equal(bv, pv))
+    if not identical:
+        raise RuntimeError("batched output differs from per-array output")
+    return {"workload": "4096 segments, lognormal sizes (median 32K, sigma 1.18, clipped 1K-4M), u32 keys + u32 "
+                        "values, uniform keys (seed 10)", "keys": n, "segments": len(sizes),
+            "batched_gkeys_per_s": n / t_batch / 1e6, "batched_ms": t_batch, "cuda_graph": True,
+            "per_array_gkeys_per_s": n / t_per / 1e6, "per_array_ms": t_per, "speedup": t_per / t_batch,
+            "identical_output": identical, "tile_variant": osw.os_get_tile_config_bucket(32, 4, osw.os_size_bucket(n // len(sizes)))}
+
+
+def measure_serving(torch, dev, count: int):
+    """Continuous batching of a Poisson request stream (sizes log-uniform
+    16K-64M keys, key types 60/25/15 % u32/u64/f32 with u32 values, 40 GB
+    device budget, seed 11): capacity first (every request present at once),
+    then the offered load at 0.7x that capacity in real time; p50/p99 latency
+    from arrival to completion."""
+    from paper_2206_01784_gb300 import serve
+
+    srv = serve.Server(budget_bytes=40 * 10**9, device=dev)
+    probe = serve.make_requests(count, seed=11, rate_per_s=1.0)
+    for r in probe:
+        r.arrival = 0.0
+    cap = srv.run(probe, realtime=False)
+    mean_keys = sum(r.n for r in probe) / len(probe)
+    capacity_rps = cap["gkeys_per_s"] * 1e9 / mean_keys
+    reqs = serve.make_requests(count, seed=11, rate_per_s=0.7 * capacity_rps)
+    st = srv.run(reqs, realtime=True)
+    return {"workload": f"{count} requests, Poisson arrivals at 0.7x measured capacity, sizes log-uniform 16K-64M, "
+                        "u32/u64/f32 keys 60/25/15 % + u32 values, 40 GB budget, inputs copied from pinned host "
+                        "memory, seed 11",
+            "capacity_gkeys_per_s": cap["gkeys_per_s"], "offered_requests_per_s": 0.7 * capacity_rps,
+            "gkeys_per_s": st["gkeys_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "mean_ms": st["mean_ms"], "batches": st["batches"], "mean_batch_requests": st["mean_batch_requests"],
+            "keys": st["keys"]}
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -351,6 +442,12 @@ def main():
         if not ok:
             raise RuntimeError("end-to-end result differs from the device result")
 
+    batched = serving = None
+    if world == 1 and not args.no_extras:
+        batched = measure_batch(torch, osw, workload, np, dev)
+        if args.serve_requests > 0:
+            serving = measure_serving(torch, dev, args.serve_requests)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = n // 2
@@ -370,6 +467,7 @@ def main():
                        "l2": "no flush: 2 GiB of inputs per step, larger than L2"},
             "roofline": roofline, "roofline_step": step_roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "gpu": torch.cuda.get_device_name(dev),
+            "batched": batched, "serving": serving,
             "paper_context": "A100-80GB: 29.4 GKey/s, 256M u32 keys only (different hardware and workload)",
         }
         print(json.dumps(line), flush=True)
