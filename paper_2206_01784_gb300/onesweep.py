@@ -98,6 +98,15 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.os_set_tile_config_bucket.argtypes = [i32, i32, i32, i32]
     lib.os_get_tile_config_bucket.restype = i32
     lib.os_get_tile_config_bucket.argtypes = [i32, i32, i32]
+    lib.os_mlp_param_count.restype = i32
+    lib.os_mlp_param_count.argtypes = [i32, i32]
+    lib.os_mlp_forward.restype = i32
+    lib.os_mlp_forward.argtypes = [vp, i32, i32, vp, i32, vp, vp]
+    lib.os_mlp_loss_grad.restype = i32
+    lib.os_mlp_loss_grad.argtypes = [vp, i32, i32, vp, vp, i32, vp, vp, vp]
+    lib.os_mlp_adam_step.restype = i32
+    lib.os_mlp_adam_step.argtypes = [vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_float, i32, vp]
     lib.os_profile_start.restype = i32
     lib.os_profile_start.argtypes = [i32]
     lib.os_profile_stop.restype = i32
@@ -202,6 +211,22 @@ def os_set_tile_config_bucket(key_bits: int, value_bytes: int, bucket: int, cfg:
 
 def os_get_tile_config_bucket(key_bits: int, value_bytes: int, bucket: int) -> int:
     return int(load().os_get_tile_config_bucket(key_bits, value_bytes, bucket))
+
+
+def os_mlp_param_count(features: int, hidden: int) -> int:
+    return int(load().os_mlp_param_count(features, hidden))
+
+
+def os_mlp_forward(params, features, hidden, x, n, y, stream) -> int:
+    return int(load().os_mlp_forward(params, features, hidden, x, n, y, stream))
+
+
+def os_mlp_loss_grad(params, features, hidden, x, t, n, grads, loss, stream) -> int:
+    return int(load().os_mlp_loss_grad(params, features, hidden, x, t, n, grads, loss, stream))
+
+
+def os_mlp_adam_step(params, grads, m, v, count, lr, beta1, beta2, eps, step, stream) -> int:
+    return int(load().os_mlp_adam_step(params, grads, m, v, count, lr, beta1, beta2, eps, step, stream))
 
 
 def os_profile_start(capacity: int) -> int:

@@ -104,10 +104,14 @@ class Admission:
     ``take(now)`` returns the batches to launch: {key_type: [requests]}, each
     group already holding its reservation in the arena (``reservations``)."""
 
-    def __init__(self, arena: Arena, workspace_bytes, max_batch_keys: int = 1 << 30):
+    def __init__(self, arena: Arena, workspace_bytes, max_batch_keys: int = 1 << 30, order=None):
+        """order: None for first-come-first-served, or a callable mapping the
+        arrived waiting requests to {id(request): priority} (lower first), as
+        learned.CostModel.priority does with predicted device times."""
         self.arena = arena
         self.workspace_bytes = workspace_bytes
         self.max_batch_keys = max_batch_keys
+        self.order = order
         self.waiting: list[Request] = []
 
     def arrive(self, req: Request) -> None:
@@ -131,15 +135,19 @@ class Admission:
         groups: dict[str, list[Request]] = {}
         order: list[str] = []
         admitted = 0
-        for r in self.waiting:
-            if r.arrival > now:
-                break
+        arrived = [r for r in self.waiting if r.arrival <= now]
+        if self.order is not None and arrived:
+            prio = self.order(arrived)
+            arrived = sorted(arrived, key=lambda r: (prio[id(r)], r.arrival, r.rid))
+        keys_in_group: dict[str, int] = {}
+        for r in arrived:
             g = groups.setdefault(r.key_type, [])
             if not g:
                 order.append(r.key_type)
-            if sum(x.n for x in g) + r.n > self.max_batch_keys:
+            if keys_in_group.get(r.key_type, 0) + r.n > self.max_batch_keys:
                 break
             g.append(r)
+            keys_in_group[r.key_type] = keys_in_group.get(r.key_type, 0) + r.n
             admitted += 1
         out = []
         kept = 0
@@ -237,9 +245,10 @@ class Server:
         ev.record(self.copy_stream)
         return seg, ev
 
-    def run(self, requests: list[Request], tick_s: float = 0.0005, realtime: bool = True) -> dict:
+    def run(self, requests: list[Request], tick_s: float = 0.0005, realtime: bool = True, order=None,
+            max_batch_keys: int = 1 << 30) -> dict:
         torch = self.torch
-        adm = Admission(self.arena, self._workspace_bytes)
+        adm = Admission(self.arena, self._workspace_bytes, max_batch_keys=max_batch_keys, order=order)
         pending = sorted(requests, key=lambda r: r.arrival)
         for i, r in enumerate(pending):
             r.data_offset = (r.rid * 7919 * 64) % max(1, self.pool.numel())
