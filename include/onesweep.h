@@ -19,13 +19,16 @@
  *    of them. The library never allocates device memory: scratch space is the
  *    caller's workspace `ws` of at least os_sort_workspace_bytes() bytes.
  *  - Keys are raw bit patterns: uint32 (OS_KEY_U32), uint64 (OS_KEY_U64),
- *    IEEE-754 binary32 (OS_KEY_F32) or binary64 (OS_KEY_F64). Float keys are
+ *    IEEE-754 binary32 (OS_KEY_F32) or binary64 (OS_KEY_F64), two's-complement
+ *    int32 (OS_KEY_I32) or int64 (OS_KEY_I64). Signed keys are ordered as
+ *    their bits with the sign bit inverted (Section 3's "magnitude-preserving
+ *    conversion" for signed types); float keys are
  *    ordered through the bijective sign-flip (negative keys: all bits
  *    inverted; others: sign bit set), so -0.0 sorts before +0.0 and NaNs sort
  *    by bit pattern (negative NaNs first, positive NaNs last). Output keys
  *    carry the input bits unchanged.
  *  - [begin_bit, end_bit) selects the key bits sorted on (of the sign-flipped
- *    bits for float keys), 0 <= begin_bit <= end_bit <= key width. Digit
+ *    bits for float and signed keys), 0 <= begin_bit <= end_bit <= key width. Digit
  *    places are 8 bits wide, start at begin_bit and go upward; the last place
  *    is narrower when the range is not a multiple of 8. begin_bit == end_bit
  *    copies the input.
@@ -62,7 +65,9 @@ typedef enum {
     OS_KEY_U32 = 0,
     OS_KEY_U64 = 1,
     OS_KEY_F32 = 2,
-    OS_KEY_F64 = 3
+    OS_KEY_F64 = 3,
+    OS_KEY_I32 = 4,
+    OS_KEY_I64 = 5
 } os_key_type;
 
 typedef enum {

@@ -31,7 +31,7 @@ _SRC = os.path.join(_HERE, "onesweep_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
-KEY_TYPES = {"u32": 0, "u64": 1, "f32": 2, "f64": 3}
+KEY_TYPES = {"u32": 0, "u64": 1, "f32": 2, "f64": 3, "i32": 4, "i64": 5}
 RADIX_BITS = 8
 
 
@@ -90,7 +90,7 @@ def _kt(key_type: str) -> int:
 
 
 def _key_dtype(key_type: str):
-    return np.uint64 if key_type in ("u64", "f64") else np.uint32
+    return np.uint64 if key_type in ("u64", "f64", "i64") else np.uint32
 
 
 def _keys(key_type: str, keys) -> np.ndarray:
@@ -102,7 +102,7 @@ def _ptr(a) -> int | None:
 
 
 def key_bits(key_type: str) -> int:
-    return 64 if key_type in ("u64", "f64") else 32
+    return 64 if key_type in ("u64", "f64", "i64") else 32
 
 
 def to_ordered(key_type: str, bits: int) -> int:

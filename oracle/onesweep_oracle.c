@@ -15,7 +15,8 @@
  *    stability: Section 1, "LSD variants are necessarily stable");
  *  - signed / floating-point keys are first mapped to unsigned integers by an
  *    order-preserving ("magnitude-preserving") conversion, and mapped back on
- *    output (Section 3, chained scan digit-binning kernel);
+ *    output (Section 3, chained scan digit-binning kernel): for two's
+ *    complement keys the sign bit is inverted;
  *  - per-place digit histograms over the whole input (Section 3, phase 1 and
  *    Figure 5) and their exclusive prefix sums, the global bin offsets
  *    (Section 2 "Prefix sum", Section 3 phase 2);
@@ -43,11 +44,11 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { ORC_U32 = 0, ORC_U64 = 1, ORC_F32 = 2, ORC_F64 = 3 };
+enum { ORC_U32 = 0, ORC_U64 = 1, ORC_F32 = 2, ORC_F64 = 3, ORC_I32 = 4, ORC_I64 = 5 };
 
 /* Key width in bits for a key type. */
 int orc_key_bits(int key_type) {
-    return (key_type == ORC_U64 || key_type == ORC_F64) ? 64 : 32;
+    return (key_type == ORC_U64 || key_type == ORC_F64 || key_type == ORC_I64) ? 64 : 32;
 }
 
 /*
@@ -59,6 +60,10 @@ int orc_key_bits(int key_type) {
  * non-negative number above every negative one.
  */
 uint64_t orc_to_ordered(int key_type, uint64_t bits) {
+    /* two's-complement keys: inverting the sign bit puts negative numbers
+       below non-negative ones and keeps the order within each */
+    if (key_type == ORC_I32) return (uint32_t)bits ^ 0x80000000u;
+    if (key_type == ORC_I64) return bits ^ 0x8000000000000000ULL;
     if (key_type == ORC_F32) {
         uint32_t b = (uint32_t)bits;
         return (b & 0x80000000u) ? (uint32_t)~b : (b | 0x80000000u);
@@ -72,6 +77,8 @@ uint64_t orc_to_ordered(int key_type, uint64_t bits) {
 
 /* Inverse of orc_to_ordered (applied when keys are written out). */
 uint64_t orc_from_ordered(int key_type, uint64_t u) {
+    if (key_type == ORC_I32) return (uint32_t)u ^ 0x80000000u;
+    if (key_type == ORC_I64) return u ^ 0x8000000000000000ULL;
     if (key_type == ORC_F32) {
         uint32_t v = (uint32_t)u;
         return (v & 0x80000000u) ? (v & 0x7FFFFFFFu) : (uint32_t)~v;

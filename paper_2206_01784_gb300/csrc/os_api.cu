@@ -142,14 +142,28 @@ size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 int key_bits_of(int key_type) {
   switch (key_type) {
     case OS_KEY_U32:
-    case OS_KEY_F32: return 32;
+    case OS_KEY_F32:
+    case OS_KEY_I32: return 32;
     case OS_KEY_U64:
-    case OS_KEY_F64: return 64;
+    case OS_KEY_F64:
+    case OS_KEY_I64: return 64;
     default: return 0;
   }
 }
 
 bool is_float(int key_type) { return key_type == OS_KEY_F32 || key_type == OS_KEY_F64; }
+
+// Signed keys sort as their bits with the sign bit inverted (two's complement
+// order). Only the most significant place holds the sign bit, so instead of
+// transforming keys, that place's digit gets its high bit inverted - when the
+// sorted range reaches the sign bit.
+uint32_t signed_top_xor(int key_type, int begin_bit, int end_bit) {
+  const int kb = key_bits_of(key_type);
+  if ((key_type != OS_KEY_I32 && key_type != OS_KEY_I64) || end_bit != kb || end_bit <= begin_bit) return 0u;
+  const int places = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
+  const int top_width = end_bit - (begin_bit + kRadixBits * (places - 1));
+  return 1u << (top_width - 1);
+}
 
 struct Plan {
   int key_bits = 0;
@@ -234,6 +248,7 @@ int run_histogram(const Plan& plan, int key_type, const void* keys, uint64_t n, 
   h.clear = clear_slab0 ? reinterpret_cast<uint32_t*>(ws + plan.layout.status_offset[0]) : nullptr;
   h.clear_words = clear_slab0 ? (uint64_t)plan.tiles * kRadix : 0;
   h.skew = reinterpret_cast<uint32_t*>(ws) + kSkewWord;
+  h.top_xor = signed_top_xor(key_type, begin_bit, end_bit);
   const int sms = device_sm_count();
   if (sms <= 0) return OS_ERR_CUDA;
   const int slot = prof_begin(0, -1, s);
@@ -329,6 +344,7 @@ int run_sort(int key_type, const void* keys_in, void* keys_out, const uint32_t* 
     a.spin_limit = g_spin_limit;
     a.fault_tile = g_fault_tile;
     a.skew_flags = header + kSkewWord + pass;
+    a.digit_xor = pass == plan.places - 1 ? signed_top_xor(key_type, begin_bit, end_bit) : 0u;
     if (pass >= 8) {
       // more than 8 passes cannot happen with 8-bit digits of <= 64-bit keys
       return OS_ERR_INVALID_ARG;
@@ -483,6 +499,7 @@ int run_batch(int key_type, const void* keys_in, void* keys_out, const uint32_t*
   b.seg_hist = reinterpret_cast<uint32_t*>(w + bp.seg_hist);
   b.seg_bin_offsets = reinterpret_cast<uint32_t*>(w + bp.seg_bin_offsets);
   b.seg_skew = reinterpret_cast<uint32_t*>(w + bp.seg_skew);
+  b.top_xor = signed_top_xor(key_type, begin_bit, end_bit);
   b.error = header;
   b.clear = reinterpret_cast<uint32_t*>(w + bp.status[0]);
   b.clear_words = bp.max_tiles * kRadix;
@@ -536,6 +553,7 @@ int run_batch(int key_type, const void* keys_in, void* keys_out, const uint32_t*
     a.total_tiles = b.totals;
     a.skew_flags = b.seg_skew + pass;
     a.skew_stride = (uint32_t)bp.places;
+    a.digit_xor = pass == bp.places - 1 ? b.top_xor : 0u;
     slot = prof_begin(1, pass, s);
     e = launch_binning(bp.key_bits, pairs, bp.bucket, a, s);
     prof_end(slot, s);

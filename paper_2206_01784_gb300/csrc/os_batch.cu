@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kSegHistThreads) batch_histogram_kernel(BatchA
 #pragma unroll
         for (int u = 0; u < kSegHistKpt; ++u) {
           if (!v[u]) continue;
-          const uint32_t d = digit_of(k[u], shift, mask);
+          const uint32_t d = digit_of(k[u], shift, mask, pl == p - 1 ? b.top_xor : 0u);
           if (run_len != 0 && d == run_digit) {
             ++run_len;
           } else {
@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(LocalConfig<KBITS>::NT) batch_local_sort_kerne
     const int shift = b.begin_bit + 8 * pass;
     const int width = min(8, b.end_bit - shift);
     const uint32_t mask = (1u << width) - 1u;
+    const uint32_t dxor = pass == b.num_places - 1 ? b.top_xor : 0u;
     for (int i = tid; i < 2 * NW * kRadix; i += NT) whist[i] = 0;
     __syncthreads();  // staged keys (or the previous pass's scatter) visible
     K key[IPT];
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(LocalConfig<KBITS>::NT) batch_local_sort_kerne
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       const bool valid = wbase + i * 32 < len;
-      rank[i] = wlms_rank<false>(wh, digit_of(key[i], shift, mask), valid, lane_bit, true);
+      rank[i] = wlms_rank<false>(wh, digit_of(key[i], shift, mask, dxor), valid, lane_bit, true);
     }
     __syncthreads();
     uint32_t total = 0;
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(LocalConfig<KBITS>::NT) batch_local_sort_kerne
     for (int i = 0; i < IPT; ++i) {
       const uint32_t idx = wbase + i * 32;
       const bool valid = idx < len;
-      pos[i] = valid ? wh[digit_of(key[i], shift, mask)].y + rank[i] : 0u;
+      pos[i] = valid ? wh[digit_of(key[i], shift, mask, dxor)].y + rank[i] : 0u;
       if (PAIRS) val[i] = valid ? vbuf[idx] : 0u;
     }
     __syncthreads();  // every read of the old order is done

@@ -162,6 +162,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int shift = a.shift;
   const uint32_t mask = a.mask;
+  const uint32_t dxor = a.digit_xor;
   const uint32_t tile = c.tile, count = c.count;
 
   // the next pass's status counters of this tile start at N
@@ -197,7 +198,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
     if (valid) differ |= (key[i] ^ first) & digit_bits;
   }
   const bool homogeneous = __syncthreads_or(differ != 0) == 0;
-  const uint32_t d0 = digit_of(first, shift, mask);
+  const uint32_t d0 = digit_of(first, shift, mask, dxor);
 
   uint32_t digit_count = 0;  // thread d < 256: keys of digit d in this tile
 
@@ -219,7 +220,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
     for (int i = 0; i < IPT; ++i) {
       const bool valid = FULL || wbase + i * 32 < count;
       const bool smask = (RANK == kRankHybrid || (RANK == kRankAdaptive && !c.skewed)) && (i & 1);
-      const uint32_t r = wlms_rank<FULL>(wh, digit_of(key[i], shift, mask), valid, lane_bit, smask);
+      const uint32_t r = wlms_rank<FULL>(wh, digit_of(key[i], shift, mask, dxor), valid, lane_bit, smask);
       if (i & 1)
         rank2[i / 2] |= r << 16;
       else
@@ -254,7 +255,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
     for (int i = 0; i < IPT; ++i) {
       const bool valid = FULL || wbase + i * 32 < count;
       const uint32_t r = (i & 1) ? (rank2[i / 2] >> 16) : (rank2[i / 2] & 0xFFFFu);
-      const uint32_t p = valid ? wh[digit_of(key[i], shift, mask)].y + r : 0u;
+      const uint32_t p = valid ? wh[digit_of(key[i], shift, mask, dxor)].y + r : 0u;
       if (valid) kt[p] = key[i];
       if (PAIRS) {
         if (i & 1)
@@ -341,7 +342,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
       const uint32_t j = i * NT + tid;
       if (FULL || j < count) {
         const K k = kt[j];
-        const uint32_t g = gbase[digit_of(k, shift, mask)] + j;
+        const uint32_t g = gbase[digit_of(k, shift, mask, dxor)] + j;
         if (g < out_len) {
           keys_out[g] = store_transform<FLIP>(k);
           if (PAIRS) vals_out[g] = vt[j];

@@ -52,11 +52,14 @@ __device__ __forceinline__ uint64_t flip_from_ordered(uint64_t u) {
   return u ^ m;
 }
 
-__device__ __forceinline__ uint32_t digit_of(uint32_t u, int shift, uint32_t mask) {
-  return (u >> shift) & mask;
+// Digit of a key at the place starting at bit `shift`, `mask` wide. For
+// signed keys the top place's digit has its high bit inverted (`x`), which
+// orders negative keys before non-negative ones; x = 0 otherwise.
+__device__ __forceinline__ uint32_t digit_of(uint32_t u, int shift, uint32_t mask, uint32_t x = 0u) {
+  return ((u >> shift) & mask) ^ x;
 }
-__device__ __forceinline__ uint32_t digit_of(uint64_t u, int shift, uint32_t mask) {
-  return (uint32_t)(u >> shift) & mask;
+__device__ __forceinline__ uint32_t digit_of(uint64_t u, int shift, uint32_t mask, uint32_t x = 0u) {
+  return ((uint32_t)(u >> shift) & mask) ^ x;
 }
 
 // ---------------------------------------------------------------- memory ops

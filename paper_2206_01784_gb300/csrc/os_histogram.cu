@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(kHistThreads, 1) histogram_kernel(HistArgs a) 
 #pragma unroll
     for (int pl = 0; pl < P; ++pl) {
       if (pl < p) {
-        const uint32_t d = digit_of(o, a.begin_bit + 8 * pl, pl == p - 1 ? last_mask : 0xFFu);
+        const uint32_t d =
+            digit_of(o, a.begin_bit + 8 * pl, pl == p - 1 ? last_mask : 0xFFu, pl == p - 1 ? a.top_xor : 0u);
         atomicAdd(mine + (pl * kRadix + d) * C, 1u);
       }
     }

@@ -22,6 +22,7 @@ struct HistArgs {
   uint32_t* clear;           // words to zero on the way (status slab of pass 0), may be null
   uint64_t clear_words;
   uint32_t* skew;            // [p] set to 1 where one digit holds over 1/16 of the keys (may be null)
+  uint32_t top_xor;          // signed keys: high bit of the top place's digit inverted (else 0)
 };
 
 // Phase 3, one digit-binning pass (Section 3, "Chained scan digit-binning kernel").
@@ -58,6 +59,7 @@ struct PassArgs {
   // segment s (0 for one array) is skew_flags[s * skew_stride].
   const uint32_t* skew_flags;
   uint32_t skew_stride;
+  uint32_t digit_xor;            // signed keys, top place: invert the digit's high bit (else 0)
 };
 
 // Segmented sort: the plan, per-segment histograms and the one-block sort of
@@ -88,6 +90,7 @@ struct BatchArgs {
   uint32_t* seg_hist;            // [S][p][256] zeroed
   uint32_t* seg_bin_offsets;     // [S][p][256]
   uint32_t* seg_skew;            // [S][p] skewed-place flags
+  uint32_t top_xor;              // signed keys: high bit of the top place's digit inverted (else 0)
   uint32_t* error;
   uint32_t* clear;               // status slab of the first pass, to zero
   uint64_t clear_words;

@@ -15,9 +15,10 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libonesweep.so")
 
-OS_KEY_U32, OS_KEY_U64, OS_KEY_F32, OS_KEY_F64 = 0, 1, 2, 3
-KEY_TYPES = {"u32": OS_KEY_U32, "u64": OS_KEY_U64, "f32": OS_KEY_F32, "f64": OS_KEY_F64}
-KEY_BITS = {OS_KEY_U32: 32, OS_KEY_U64: 64, OS_KEY_F32: 32, OS_KEY_F64: 64}
+OS_KEY_U32, OS_KEY_U64, OS_KEY_F32, OS_KEY_F64, OS_KEY_I32, OS_KEY_I64 = 0, 1, 2, 3, 4, 5
+KEY_TYPES = {"u32": OS_KEY_U32, "u64": OS_KEY_U64, "f32": OS_KEY_F32, "f64": OS_KEY_F64, "i32": OS_KEY_I32,
+             "i64": OS_KEY_I64}
+KEY_BITS = {OS_KEY_U32: 32, OS_KEY_U64: 64, OS_KEY_F32: 32, OS_KEY_F64: 64, OS_KEY_I32: 32, OS_KEY_I64: 64}
 
 OS_OK, OS_ERR_INVALID_ARG, OS_ERR_TOO_LARGE, OS_ERR_WORKSPACE, OS_ERR_CUDA, OS_ERR_TIMEOUT = range(6)
 OS_ERR_SCRATCH_LIMIT = 6
@@ -250,7 +251,8 @@ def _torch():
 
 
 def key_type_of(t, key_type: str | int | None = None) -> int:
-    """Key type for a tensor: explicit, or float32/float64 by dtype, else unsigned by width."""
+    """Key type for a tensor: explicit, or by dtype (float32/64, int32/64 as
+    signed, other 4/8-byte types as unsigned)."""
     torch = _torch()
     if key_type is not None:
         return KEY_TYPES[key_type] if isinstance(key_type, str) else int(key_type)
@@ -258,6 +260,10 @@ def key_type_of(t, key_type: str | int | None = None) -> int:
         return OS_KEY_F32
     if t.dtype == torch.float64:
         return OS_KEY_F64
+    if t.dtype == torch.int32:
+        return OS_KEY_I32
+    if t.dtype == torch.int64:
+        return OS_KEY_I64
     if t.element_size() == 4:
         return OS_KEY_U32
     if t.element_size() == 8:

@@ -144,8 +144,8 @@ class Admission:
             g = groups.setdefault(r.key_type, [])
             if not g:
                 order.append(r.key_type)
-            if keys_in_group.get(r.key_type, 0) + r.n > self.max_batch_keys:
-                break
+            if g and keys_in_group.get(r.key_type, 0) + r.n > self.max_batch_keys:
+                break  # a request alone may exceed the cap; otherwise the group is full
             g.append(r)
             keys_in_group[r.key_type] = keys_in_group.get(r.key_type, 0) + r.n
             admitted += 1

@@ -123,13 +123,13 @@ def normal(n: int, seed: int, stream: int = 0) -> np.ndarray:
     return out
 
 
-KEY_TYPES = ("u32", "u64", "f32", "f64")
+KEY_TYPES = ("u32", "u64", "f32", "f64", "i32", "i64")
 DISTRIBUTIONS = ("uniform", "and2", "and3", "and4", "and5", "and8", "and16", "const", "normal")
 
 
 def keys(key_type: str, dist: str, n: int, seed: int) -> np.ndarray:
-    """Key bits for ``key_type`` (uint32 for u32/f32, uint64 for u64/f64)."""
-    wide = key_type in ("u64", "f64")
+    """Key bits for ``key_type`` (uint32 for 32-bit types, uint64 for 64-bit)."""
+    wide = key_type in ("u64", "f64", "i64")
     if dist == "normal":
         if key_type == "f32":
             return f32_normal_bits(n, seed)

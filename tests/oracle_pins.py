@@ -100,7 +100,14 @@ def pin_tile_counts():
                                                 minlength=256)) for t in range(c.shape[0]))
 
 
-PINS = [pin_exclusive_sum, pin_flag_scan, pin_sort_numpy, pin_float, pin_histograms, pin_float_np,
+def pin_signed():
+    bits = workload.keys("i32", "uniform", 4000, seed=17)
+    ko, vo = oracle.sort("i32", bits, workload.iota_u32(bits.size))
+    perm = np.argsort(bits.view(np.int32), kind="stable")
+    return bool(np.array_equal(vo, perm.astype(np.uint32)) and np.array_equal(ko, bits[perm]))
+
+
+PINS = [pin_signed, pin_exclusive_sum, pin_flag_scan, pin_sort_numpy, pin_float, pin_histograms, pin_float_np,
         pin_tile_counts]
 
 

@@ -17,7 +17,7 @@ from paper_2206_01784_gb300 import workload  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-KB = {"u32": 32, "u64": 64, "f32": 32, "f64": 64}
+KB = {"u32": 32, "u64": 64, "f32": 32, "f64": 64, "i32": 32, "i64": 64}
 
 
 def _dev():
@@ -65,7 +65,7 @@ def edge_sizes(kt, pairs):
     return [0, 1, 2, 31, 33, cap - 1, cap, cap + 1, 0, t - 1, t, t + 1, 3 * t + 7, 1000, 0, 5, 2 * cap + 3]
 
 
-@pytest.mark.parametrize("kt", ["u32", "u64", "f32", "f64"])
+@pytest.mark.parametrize("kt", ["u32", "u64", "f32", "f64", "i32", "i64"])
 @pytest.mark.parametrize("pairs", [False, True])
 def test_batch_edge_segments(kt, pairs):
     sizes = edge_sizes(kt, pairs)

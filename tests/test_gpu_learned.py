@@ -77,7 +77,9 @@ def test_shortest_predicted_first_beats_fifo_on_a_burst():
     X, T = learned.collect(sizes_log2=range(10, 23, 2), reps=2)
     model = learned.CostModel(hidden=32, seed=0)
     model.fit(X, T, steps=2500, lr=3e-3)
-    srv = serve.Server(budget_bytes=600 << 20, pool_words=1 << 24)
+    # a 256 MB budget and 1M-key batches serialise the burst, so the order of
+    # admission decides how long small requests wait
+    srv = serve.Server(budget_bytes=256 << 20, pool_words=1 << 24)
 
     def burst():
         reqs = serve.make_requests(200, seed=9, rate_per_s=1.0, lo_log2=10, hi_log2=22)
@@ -85,8 +87,10 @@ def test_shortest_predicted_first_beats_fifo_on_a_burst():
             r.arrival = 0.0
         return reqs
 
-    fifo = srv.run(burst(), realtime=False, max_batch_keys=1 << 22)
-    sjf = srv.run(burst(), realtime=False, max_batch_keys=1 << 22, order=model.priority)
+    fifo = srv.run(burst(), realtime=False, max_batch_keys=1 << 20)
+    sjf = srv.run(burst(), realtime=False, max_batch_keys=1 << 20, order=model.priority)
     # the same work, but small requests no longer wait behind large ones
+    # (measured on GB300: mean 9.9 ms against 19.6 ms, median 6.0 against 20.8)
     assert sjf["keys"] == fifo["keys"]
-    assert sjf["mean_ms"] < 0.8 * fifo["mean_ms"], (sjf["mean_ms"], fifo["mean_ms"])
+    assert sjf["mean_ms"] < 0.7 * fifo["mean_ms"], (sjf["mean_ms"], fifo["mean_ms"])
+    assert sjf["p50_ms"] < 0.5 * fifo["p50_ms"], (sjf["p50_ms"], fifo["p50_ms"])

@@ -16,7 +16,7 @@ from paper_2206_01784_gb300 import workload  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-KB = {"u32": 32, "u64": 64, "f32": 32, "f64": 64}
+KB = {"u32": 32, "u64": 64, "f32": 32, "f64": 64, "i32": 32, "i64": 64}
 
 
 def _dev():
@@ -70,7 +70,8 @@ def make_keys(kt, dist, n, seed):
 # ---------------------------------------------------------------- phase 1 + 2
 
 @pytest.mark.parametrize("kt,begin,end", [("u32", 0, 32), ("u32", 3, 29), ("u64", 0, 64), ("u64", 5, 50),
-                                          ("f32", 0, 32), ("f64", 0, 64), ("u32", 0, 8)])
+                                          ("f32", 0, 32), ("f64", 0, 64), ("u32", 0, 8), ("i32", 0, 32),
+                                          ("i64", 3, 64)])
 @pytest.mark.parametrize("n", [1, 3, 31, 33, 4097, 100_003, 1 << 20])
 def test_histograms_and_offsets(kt, begin, end, n):
     keys = make_keys(kt, "uniform", n, seed=n)
@@ -135,7 +136,7 @@ def test_lookback_final_status_counters():
 SIZES = [1, 2, 31, 32, 33, 1000]
 
 
-@pytest.mark.parametrize("kt", ["u32", "u64", "f32", "f64"])
+@pytest.mark.parametrize("kt", ["u32", "u64", "f32", "f64", "i32", "i64"])
 @pytest.mark.parametrize("pairs", [False, True])
 def test_sort_edge_sizes(kt, pairs):
     t = tile_keys(kt, pairs)
@@ -189,7 +190,9 @@ def test_sort_float_specials():
 
 
 @pytest.mark.parametrize("kt,begin,end", [("u32", 0, 0), ("u32", 4, 20), ("u32", 13, 31), ("u32", 7, 8),
-                                          ("u64", 5, 50), ("u64", 0, 33), ("f32", 16, 32), ("u64", 60, 64)])
+                                          ("u64", 5, 50), ("u64", 0, 33), ("f32", 16, 32), ("u64", 60, 64),
+                                          ("i32", 0, 32), ("i32", 5, 32), ("i32", 3, 31), ("i64", 0, 64),
+                                          ("i64", 7, 64), ("i64", 0, 40)])
 def test_sort_bit_ranges(kt, begin, end):
     n = 3 * tile_keys(kt, True) + 99
     keys = make_keys(kt, "uniform", n, seed=begin * 100 + end)

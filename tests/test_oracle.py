@@ -303,3 +303,20 @@ def test_generator_entropy_bands_match_table1():
         p = ones / (32.0 * n)
         est = 0.0 if p in (0.0, 1.0) else -(p * np.log2(p) + (1 - p) * np.log2(1 - p))
         assert abs(est - h) <= max(1e-3, 0.1 * h), (q, est, h)
+
+
+@pytest.mark.parametrize("kt,np_t", [("i32", np.int32), ("i64", np.int64)])
+def test_signed_sort_matches_numpy_signed_order(kt, np_t):
+    n = 30000
+    bits = workload.keys(kt, "uniform", n, seed=17)
+    ext = np.array([0, 1, -1, np.iinfo(np_t).min, np.iinfo(np_t).max], dtype=np_t).view(bits.dtype)
+    bits = np.concatenate([bits, ext, ext])
+    vals = np.arange(bits.size, dtype=np.uint32)
+    ko, vo = oracle.sort(kt, bits, vals)
+    perm = np.argsort(bits.view(np_t), kind="stable")
+    assert np.array_equal(vo, perm.astype(np.uint32))
+    assert np.array_equal(ko, bits[perm])
+    # a range below the sign bit sorts the raw sub-field
+    kb = 64 if kt == "i64" else 32
+    ko2, vo2 = oracle.sort(kt, bits, vals, 4, kb - 4)
+    assert np.array_equal(vo2, np.argsort(_field_np(bits, 4, kb - 4), kind="stable").astype(np.uint32))

@@ -31,6 +31,8 @@ MUTANTS = {
                                   "hist[place * r + digit_of(load_key(key_type, keys, i), shift, width)] += 1;"),
     "tile_index_wrong": ("counts[(i / tile) * r", "counts[(i / (tile + 1)) * r"),
     "places_start_at_zero": ("*shift = begin_bit + place * radix_bits;", "*shift = place * radix_bits;"),
+    "signed_keys_not_flipped": ("if (key_type == ORC_I32) return (uint32_t)bits ^ 0x80000000u;",
+                                "if (key_type == ORC_I32) return (uint32_t)bits;"),
 }
 
 
