@@ -204,7 +204,9 @@ __global__ void __launch_bounds__(LocalConfig<KBITS>::NT) batch_local_sort_kerne
   if (PAIRS)
     for (uint32_t i = tid; i < len; i += NT) vbuf[i] = b.vals_in[s0 + i];
 
-  uint2* wh = reinterpret_cast<uint2*>(whist) + warp * kRadix;
+  uint32_t* wcnt = whist + NW * kRadix;
+  uint32_t* wmsk = whist + warp * kRadix;
+  uint32_t* wc = wcnt + warp * kRadix;
   const uint32_t wbase = (uint32_t)warp * IPT * 32 + lane;
   const uint32_t lane_bit = 1u << lane;
   for (int pass = 0; pass < b.num_places; ++pass) {
@@ -230,18 +232,18 @@ __global__ void __launch_bounds__(LocalConfig<KBITS>::NT) batch_local_sort_kerne
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       const bool valid = wbase + i * 32 < len;
-      rank[i] = wlms_rank<false>(wh, digit_of(key[i], shift, mask, dxor), valid, lane_bit, true);
+      rank[i] = wlms_rank<false>(wmsk, wc, digit_of(key[i], shift, mask, dxor), valid, lane_bit, true);
     }
     __syncthreads();
     uint32_t total = 0;
     if (tid < kRadix)
-      for (int w = 0; w < NW; ++w) total += whist[2 * (w * kRadix + tid) + 1];
+      for (int w = 0; w < NW; ++w) total += wcnt[w * kRadix + tid];
     const uint32_t excl = block_exclusive_sum<NT>(tid < kRadix ? total : 0u, misc);
     if (tid < kRadix) {
       uint32_t run = excl;
       for (int w = 0; w < NW; ++w) {
-        const uint32_t cw = whist[2 * (w * kRadix + tid) + 1];
-        whist[2 * (w * kRadix + tid) + 1] = run;
+        const uint32_t cw = wcnt[w * kRadix + tid];
+        wcnt[w * kRadix + tid] = run;
         run += cw;
       }
     }
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(LocalConfig<KBITS>::NT) batch_local_sort_kerne
     for (int i = 0; i < IPT; ++i) {
       const uint32_t idx = wbase + i * 32;
       const bool valid = idx < len;
-      pos[i] = valid ? wh[digit_of(key[i], shift, mask, dxor)].y + rank[i] : 0u;
+      pos[i] = valid ? wc[digit_of(key[i], shift, mask, dxor)] + rank[i] : 0u;
       if (PAIRS) val[i] = valid ? vbuf[idx] : 0u;
     }
     __syncthreads();  // every read of the old order is done

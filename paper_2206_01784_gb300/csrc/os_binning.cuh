@@ -76,7 +76,7 @@ struct BinningConfig {
   // staging buffers hold a tile plus the slack of a 16-byte-aligned span
   static constexpr size_t kbuf_bytes = (size_t)T * sizeof(K) + 16;
   static constexpr size_t vbuf_bytes = PAIRS ? (size_t)T * 4 + 16 : 0;
-  static constexpr size_t whist_bytes = (size_t)NW * kRadix * 8;  // [NW][256] {lane mask, count}
+  static constexpr size_t whist_bytes = (size_t)NW * kRadix * 8;  // [NW][256] lane masks, then [NW][256] counts
   static constexpr size_t small_bytes = 2 * kRadix * 4 + 64 * 4 + 2 * 8;
   static constexpr size_t smem_bytes = kbuf_bytes + vbuf_bytes + whist_bytes + small_bytes;
 };
@@ -121,25 +121,29 @@ struct TileCtx {
 
 // Warp-level multi-split ranking of one 32-key batch (step 4). Returns the
 // key's rank among the keys of the same digit in this warp's part of the tile.
+// msk / cnt: this warp's 256 lane-mask words and 256 running digit counts
+// (separate 32-bit arrays, so random digits spread over all 32 banks).
 template <bool FULL>
-__device__ __forceinline__ uint32_t wlms_rank(uint2* wh, uint32_t d, bool valid, uint32_t lane_bit, bool smask) {
+__device__ __forceinline__ uint32_t wlms_rank(uint32_t* msk, uint32_t* cnt, uint32_t d, bool valid, uint32_t lane_bit,
+                                              bool smask) {
   uint32_t peers, old;
   if (smask) {
     // every lane ORs its bit into its digit's mask word; OR commutes, so the
     // mask read back is exactly the lanes sharing the digit
-    if (valid) atomicOr(&wh[d].x, lane_bit);
+    if (valid) atomicOr(msk + d, lane_bit);
     __syncwarp();
-    const uint2 mc = valid ? wh[d] : make_uint2(0u, 0u);
-    peers = mc.x;
-    old = mc.y;
+    peers = valid ? msk[d] : 0u;
   } else {
     const uint32_t valid_mask = FULL ? 0xFFFFFFFFu : __ballot_sync(0xFFFFFFFFu, valid);
     peers = digit_peers(d, valid, valid_mask);
-    old = valid ? wh[d].y : 0u;
   }
+  old = valid ? cnt[d] : 0u;
   const uint32_t below = __popc(peers & lanemask_lt());
   __syncwarp();
-  if (valid && below == 0) wh[d] = make_uint2(0u, old + __popc(peers));
+  if (valid && below == 0) {
+    if (smask) msk[d] = 0u;
+    cnt[d] = old + __popc(peers);
+  }
   __syncwarp();
   return old + below;
 }
@@ -152,8 +156,9 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
 
   K* kt = reinterpret_cast<K*>(smem) + c.koff;
   uint32_t* vt = reinterpret_cast<uint32_t*>(smem + C::kbuf_bytes) + c.voff;
-  // [NW][256] pairs {lane mask of the current batch, running count}
+  // [NW][256] lane masks of the current batch, then [NW][256] running counts
   uint32_t* whist = reinterpret_cast<uint32_t*>(smem + C::kbuf_bytes + C::vbuf_bytes);
+  uint32_t* wcnt = whist + NW * kRadix;
   uint32_t* dstart = whist + 2 * NW * kRadix;  // [256] tile-local start of each digit's bin
   uint32_t* gbase = dstart + kRadix;           // [256] segment index of local position 0 of each bin
   uint32_t* misc = gbase + kRadix;             // [64] scan scratch
@@ -213,14 +218,15 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
   } else {
     // 4. warp-level multi-split ranking; rank = keys of the same digit before
     //    this one in the warp's part of the tile
-    uint2* wh = reinterpret_cast<uint2*>(whist) + warp * kRadix;
+    uint32_t* wmsk = whist + warp * kRadix;
+    uint32_t* wc = wcnt + warp * kRadix;
     uint32_t rank2[IPT / 2 + 1];  // two 16-bit ranks per register (ranks < T <= 2^16)
     const uint32_t lane_bit = 1u << lane;
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       const bool valid = FULL || wbase + i * 32 < count;
-      const bool smask = (RANK == kRankHybrid || (RANK == kRankAdaptive && !c.skewed)) && (i & 1);
-      const uint32_t r = wlms_rank<FULL>(wh, digit_of(key[i], shift, mask, dxor), valid, lane_bit, smask);
+      const bool smask = RANK == kRankHybrid && (i & 1);
+      const uint32_t r = wlms_rank<FULL>(wmsk, wc, digit_of(key[i], shift, mask, dxor), valid, lane_bit, smask);
       if (i & 1)
         rank2[i / 2] |= r << 16;
       else
@@ -231,7 +237,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
     // 5. tile digit counts, publish L, per-warp exclusive offsets
     if (tid < kRadix) {
 #pragma unroll
-      for (int w = 0; w < NW; ++w) digit_count += whist[2 * (w * kRadix + tid) + 1];
+      for (int w = 0; w < NW; ++w) digit_count += wcnt[w * kRadix + tid];
       if (publish)
         st_relaxed_gpu(status + tid, ((chain_head ? kFlagGlobal : kFlagLocal) << kStatusShift) | digit_count);
     }
@@ -240,8 +246,8 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
       uint32_t run = excl;
 #pragma unroll
       for (int w = 0; w < NW; ++w) {
-        const uint32_t cw = whist[2 * (w * kRadix + tid) + 1];
-        whist[2 * (w * kRadix + tid) + 1] = run;
+        const uint32_t cw = wcnt[w * kRadix + tid];
+        wcnt[w * kRadix + tid] = run;
         run += cw;
       }
       dstart[tid] = excl;
@@ -255,7 +261,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
     for (int i = 0; i < IPT; ++i) {
       const bool valid = FULL || wbase + i * 32 < count;
       const uint32_t r = (i & 1) ? (rank2[i / 2] >> 16) : (rank2[i / 2] & 0xFFFFu);
-      const uint32_t p = valid ? wh[digit_of(key[i], shift, mask, dxor)].y + r : 0u;
+      const uint32_t p = valid ? wc[digit_of(key[i], shift, mask, dxor)] + r : 0u;
       if (valid) kt[p] = key[i];
       if (PAIRS) {
         if (i & 1)
@@ -441,10 +447,21 @@ __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS, CFG>::NT, BinningC
       for (uint32_t i = tid; i < c.count; i += NT) vbuf[i] = a.vals_in[c.start + i];
   }
 
-  if (c.count == (uint32_t)T)
-    binning_tile<KBITS, PAIRS, CFG, RANK, FLIP, true>(a, smem, c);
-  else
-    binning_tile<KBITS, PAIRS, CFG, RANK, FLIP, false>(a, smem, c);
+  // adaptive ranking: one uniform branch per tile between two whole bodies
+  // (ballots for a skewed place, the hybrid otherwise)
+  constexpr int R0 = RANK == kRankAdaptive ? kRankHybrid : RANK;
+  const bool ballots = RANK == kRankAdaptive && c.skewed;
+  if (c.count == (uint32_t)T) {
+    if (ballots)
+      binning_tile<KBITS, PAIRS, CFG, kRankBallot, FLIP, true>(a, smem, c);
+    else
+      binning_tile<KBITS, PAIRS, CFG, R0, FLIP, true>(a, smem, c);
+  } else {
+    if (ballots)
+      binning_tile<KBITS, PAIRS, CFG, kRankBallot, FLIP, false>(a, smem, c);
+    else
+      binning_tile<KBITS, PAIRS, CFG, R0, FLIP, false>(a, smem, c);
+  }
 }
 
 template <int KBITS, bool PAIRS, int CFG, int RANK, int FLIP, bool SEG>
