@@ -406,38 +406,76 @@ def main():
                      "histogram_avg_ms": statistics.mean(hist_ms) if hist_ms else None,
                      "binning_avg_ms": bin_avg}
 
-    # end to end: pinned host buffers, H2D of the inputs and D2H of the result in the timed region
+    # End to end through the C ABI: every step uploads its keys (and values)
+    # from pinned host memory, sorts, and downloads the sorted result. Steps
+    # are pipelined the way a stream of arrays would be served: uploads, sorts
+    # and downloads run on three streams over two device buffer sets, so step
+    # i's sort overlaps step i+1's upload and step i-1's download.
     e2e = None
     if args.e2e_steps > 0:
         hk = torch.from_numpy(keys_np.view(np.int32)).pin_memory()
         hv = torch.from_numpy(vals_np.view(np.int32)).pin_memory()
         hko = torch.empty_like(hk).pin_memory()
         hvo = torch.empty_like(hv).pin_memory()
-
-        def e2e_step():
-            keys.copy_(hk, non_blocking=True)
-            if pairs:
-                vals.copy_(hv, non_blocking=True)
-            step()
-            hko.copy_(keys_out, non_blocking=True)
-            if pairs:
-                hvo.copy_(vals_out, non_blocking=True)
-
-        e2e_step()
+        sets = [(keys, vals, keys_out, vals_out, ws)]
+        sets.append((torch.empty_like(keys), torch.empty_like(vals), torch.empty_like(keys_out),
+                     torch.empty_like(vals_out), torch.empty_like(ws)))
+        up_s, sort_s, down_s = (torch.cuda.Stream(dev) for _ in range(3))
+        ev = lambda: torch.cuda.Event()  # noqa: E731
+        uploaded, sorted_, downloaded = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+        for e in sorted_ + downloaded:
+            e.record(torch.cuda.current_stream(dev))
         barrier()
+
+        def e2e_step(i):
+            b = i % 2
+            k, v, ko, vo, w = sets[b]
+            with torch.cuda.stream(up_s):
+                up_s.wait_event(sorted_[b])  # the sort two steps back has read this input set
+                k.copy_(hk, non_blocking=True)
+                if pairs:
+                    v.copy_(hv, non_blocking=True)
+                uploaded[b].record(up_s)
+            sort_s.wait_event(uploaded[b])
+            sort_s.wait_event(downloaded[b])  # this output set was downloaded
+            if pairs:
+                rc = osw.os_sort_pairs(kt, k.data_ptr(), ko.data_ptr(), v.data_ptr(), vo.data_ptr(), n, 0, 32,
+                                       w.data_ptr(), w.numel(), sort_s.cuda_stream)
+            else:
+                rc = osw.os_sort_keys(kt, k.data_ptr(), ko.data_ptr(), n, 0, 32, w.data_ptr(), w.numel(),
+                                      sort_s.cuda_stream)
+            if rc != osw.OS_OK:
+                raise osw.OnesweepError(rc, "sort")
+            sorted_[b].record(sort_s)
+            with torch.cuda.stream(down_s):
+                down_s.wait_event(sorted_[b])
+                hko.copy_(ko, non_blocking=True)
+                if pairs:
+                    hvo.copy_(vo, non_blocking=True)
+                downloaded[b].record(down_s)
+
+        for i in range(2):
+            e2e_step(i)
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = time.perf_counter()
         e0 = torch.cuda.Event(enable_timing=True)
+        e0.record(up_s)
+        for i in range(args.e2e_steps):
+            e2e_step(i)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.e2e_steps):
-            e2e_step()
-        e1.record(stream)
+        e1.record(down_s)
+        torch.cuda.synchronize(dev)
         barrier()
-        et = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+        et_ms = max(e0.elapsed_time(e1), 0.0)
+        wall_ms = (time.perf_counter() - t0) * 1e3
+        et = torch.tensor([max(et_ms, wall_ms)], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(et, op=dist.ReduceOp.MAX)
         e2e = {"value": world * n * args.e2e_steps / (float(et.item()) / 1e3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": hk.numel() * 4 + (hv.numel() * 4 if pairs else 0),
-               "d2h_bytes_per_step": hko.numel() * 4 + (hvo.numel() * 4 if pairs else 0), "steps": args.e2e_steps}
+               "d2h_bytes_per_step": hko.numel() * 4 + (hvo.numel() * 4 if pairs else 0), "steps": args.e2e_steps,
+               "pipelined": "uploads, sorts and downloads on three streams, two device buffer sets"}
         ok = np.array_equal(hko.numpy().view(np.uint32)[:: 1 << 16], keys_out.cpu().numpy().view(np.uint32)[:: 1 << 16])
         if not ok:
             raise RuntimeError("end-to-end result differs from the device result")
