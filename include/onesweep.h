@@ -34,8 +34,10 @@
  *    copies the input.
  *  - Sorting is stable: equal keys keep their input order, and values follow
  *    their keys.
- *  - n must be below 2^30 (the chained scan keeps 30-bit counts, Section 3
- *    "Handling very large problems"); larger n returns OS_ERR_TOO_LARGE.
+ *  - n must be below 2^32 (output positions are 32-bit); larger n returns
+ *    OS_ERR_TOO_LARGE. The chained scan keeps 30-bit counts, so passes over
+ *    more than 2^28 keys run strip by strip (Section 3, "Handling very large
+ *    problems"; see os_debug_set_strip_keys).
  *  - Inputs are never modified. Input, output and workspace ranges must not
  *    overlap (OS_ERR_INVALID_ARG). Key pointers must be aligned to the key
  *    width and value pointers to 4 bytes.
@@ -73,7 +75,7 @@ typedef enum {
 typedef enum {
     OS_OK = 0,
     OS_ERR_INVALID_ARG = 1, /* bad key type, bit range, pointer, alignment or overlap */
-    OS_ERR_TOO_LARGE = 2,   /* n >= 2^30 */
+    OS_ERR_TOO_LARGE = 2,   /* n >= 2^32 */
     OS_ERR_WORKSPACE = 3,   /* workspace missing or smaller than required */
     OS_ERR_CUDA = 4,        /* a CUDA call or kernel launch failed */
     OS_ERR_TIMEOUT = 5,     /* a chained-scan look-back wait ran past its limit */
@@ -236,6 +238,19 @@ OS_API int os_get_tile_config_bucket(int key_bits, int value_bytes, int bucket);
  * limit. Process-wide setting, applied at launch time.
  */
 OS_API void os_debug_set_lookback_fault(int64_t tile, uint32_t spin_limit);
+
+/*
+ * Strip length of single-array sorts (Section 3, "Handling very large
+ * problems"): a pass over more keys than one strip runs as one binning launch
+ * per strip, each strip a chain of its own, the next strip's bins starting
+ * where the previous strip's ended. The default, 2^28 keys (rounded down to a
+ * whole number of tiles), keeps every look-back count below the 30-bit limit;
+ * tests set shorter strips to run the multi-strip path on small inputs.
+ * `keys` is clamped to [2^16, 2^28]; 0 restores the default. Returns the
+ * value set. Process-wide, applied when a sort is planned; a workspace sized
+ * for n fits any strip length.
+ */
+OS_API uint64_t os_debug_set_strip_keys(uint64_t keys);
 
 /*
  * Launch timing for benchmarks (not part of the method). os_profile_start

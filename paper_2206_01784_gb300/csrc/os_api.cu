@@ -97,12 +97,20 @@ cudaError_t launch_binning(int key_bits, bool pairs, int bucket, const PassArgs&
 
 namespace {
 
-constexpr uint64_t kMaxKeys = 1ull << 30;     // 30-bit status counter values
+// Section 3, "Handling very large problems": the chained scan keeps 30-bit
+// counts, so a pass over more than kStripKeys keys runs strip by strip (one
+// launch each, every strip its own look-back chain); 32-bit output indices
+// then bound n below 2^32.
+constexpr uint64_t kMaxKeys = 1ull << 32;
+constexpr uint64_t kStripKeys = 1ull << 28;
+constexpr uint64_t kMinStripKeys = 1ull << 16;
+uint64_t g_strip_keys = kStripKeys;  // shorter strips: os_debug_set_strip_keys
 constexpr size_t kAlign = 256;
 constexpr uint32_t kDefaultSpinLimit = 1u << 22;
 
 // Header layout: word 0 device status, word 1 done counter of the histogram
-// kernel, words 16..23 tile counters of the binning passes.
+// kernel, words 16..23 tile counters of a batch sort's binning passes (a
+// single-array sort keeps one counter per launch after the histograms).
 constexpr size_t kHeaderBytes = 256;
 constexpr size_t kDoneWord = 1;
 constexpr size_t kTileCounterWord = 16;
@@ -171,7 +179,11 @@ struct Plan {
   int bucket = 0;
   int places = 0;
   uint32_t tile = 0;
-  uint32_t tiles = 0;
+  uint32_t tiles = 0;        // tiles of a whole pass
+  uint64_t strip = 0;        // keys per strip (a multiple of the tile)
+  uint32_t strips = 0;       // strips per pass
+  size_t counters = 0;       // tile counters, one per launch
+  size_t carry = 0;          // two [256] arrays of strip bin bases
   os_workspace_layout layout{};
 };
 
@@ -187,15 +199,30 @@ int make_plan(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_
   plan->bucket = size_bucket(n);
   plan->tile = binning_tile_keys(kb, plan->pairs, plan->bucket);
   plan->tiles = (uint32_t)((n + plan->tile - 1) / plan->tile);
+  uint64_t strip = g_strip_keys / plan->tile * plan->tile;
+  if (strip == 0) strip = plan->tile;
+  plan->strip = strip;
+  plan->strips = n == 0 ? 1u : (uint32_t)((n + strip - 1) / strip);
+  // status slabs: rows for the largest launch (at most one strip of the
+  // smallest tile of any geometry, so every geometry fits)
   const uint32_t min_tile = min_tile_keys(kb, plan->pairs);
-  const uint64_t max_tiles = (n + min_tile - 1) / min_tile;
+  const uint64_t launch_keys = n < kStripKeys ? n : kStripKeys;
+  const uint64_t max_tiles = (launch_keys + min_tile - 1) / min_tile;
+  // one tile counter per launch: 8 places x strips, for any strip length the
+  // test hook allows (>= kMinStripKeys rounded down to a tile of < 2^15 keys,
+  // so longer than 2^15 keys; a workspace sized once always fits)
+  const uint64_t max_strips = n / (kMinStripKeys / 2) + 2;
   os_workspace_layout& L = plan->layout;
   std::memset(&L, 0, sizeof(L));
   size_t off = kHeaderBytes;
   L.histogram_offset = off;
   off = round_up(off + (size_t)8 * kRadix * 4);
+  plan->counters = off;
+  off = round_up(off + (size_t)8 * max_strips * 4);
   L.bin_offset_offset = off;
   off = round_up(off + (size_t)8 * kRadix * 4);
+  plan->carry = off;
+  off = round_up(off + (size_t)2 * kRadix * 4);
   const size_t slab = (size_t)max_tiles * kRadix * 4;
   L.status_offset[0] = off;
   off = round_up(off + slab);
@@ -246,7 +273,9 @@ int run_histogram(const Plan& plan, int key_type, const void* keys, uint64_t n, 
   h.offsets = reinterpret_cast<uint32_t*>(ws + plan.layout.bin_offset_offset);
   h.done_counter = reinterpret_cast<uint32_t*>(ws) + kDoneWord;
   h.clear = clear_slab0 ? reinterpret_cast<uint32_t*>(ws + plan.layout.status_offset[0]) : nullptr;
-  h.clear_words = clear_slab0 ? (uint64_t)plan.tiles * kRadix : 0;
+  // the first launch's rows (the first strip's tiles)
+  const uint64_t first_tiles = (plan.strip < n ? plan.strip : n + plan.tile - 1) / plan.tile;
+  h.clear_words = clear_slab0 ? first_tiles * kRadix : 0;
   h.skew = reinterpret_cast<uint32_t*>(ws) + kSkewWord;
   h.top_xor = signed_top_xor(key_type, begin_bit, end_bit);
   const int sms = device_sm_count();
@@ -299,8 +328,9 @@ int run_sort(int key_type, const void* keys_in, void* keys_out, const uint32_t* 
     return OS_OK;
   }
 
-  // zero: status word, done counter, tile counters, histograms
-  if (cudaMemsetAsync(w, 0, plan.layout.bin_offset_offset, s) != cudaSuccess) return OS_ERR_CUDA;
+  // zero: status word, done counter, histograms, this sort's tile counters
+  const size_t zero_bytes = plan.counters + (size_t)plan.places * plan.strips * 4;
+  if (cudaMemsetAsync(w, 0, zero_bytes, s) != cudaSuccess) return OS_ERR_CUDA;
   rc = run_histogram(plan, key_type, keys_in, n, begin_bit, end_bit, w, true, s);
   if (rc != OS_OK) return rc;
 
@@ -313,46 +343,66 @@ int run_sort(int key_type, const void* keys_in, void* keys_out, const uint32_t* 
   const bool aligned_out = reinterpret_cast<uintptr_t>(keys_out) % 16 == 0 &&
                            (!pairs || reinterpret_cast<uintptr_t>(vals_out) % 16 == 0);
 
+  const size_t kbytes_per_key = plan.key_bits / 8;
+  uint32_t* counters = reinterpret_cast<uint32_t*>(w + plan.counters);
+  uint32_t* carry = reinterpret_cast<uint32_t*>(w + plan.carry);  // two [256] arrays
+  auto strip_len = [&](uint32_t st) {
+    const uint64_t lo = (uint64_t)st * plan.strip;
+    return (uint32_t)((n - lo) < plan.strip ? (n - lo) : plan.strip);
+  };
+  auto strip_tiles = [&](uint32_t st) { return (strip_len(st) + plan.tile - 1) / plan.tile; };
+  const uint32_t launches = (uint32_t)plan.places * plan.strips;
+
   const void* src_k = keys_in;
   const uint32_t* src_v = vals_in;
   bool src_aligned = aligned_in;
+  uint32_t launch = 0;
   for (int pass = 0; pass < plan.places; ++pass) {
     // ping-pong so that the last pass writes keys_out
     const bool to_out = ((plan.places - 1 - pass) % 2) == 0;
     void* dst_k = to_out ? keys_out : alt_keys;
     uint32_t* dst_v = to_out ? vals_out : alt_vals;
-    PassArgs a{};
-    a.keys_in = src_k;
-    a.keys_out = dst_k;
-    a.vals_in = pairs ? src_v : nullptr;
-    a.vals_out = pairs ? dst_v : nullptr;
-    a.n = (uint32_t)n;
-    a.num_tiles = plan.tiles;
-    a.shift = begin_bit + kRadixBits * pass;
-    const int width = end_bit - a.shift < kRadixBits ? end_bit - a.shift : kRadixBits;
-    a.mask = (1u << width) - 1u;
-    a.flip_in = is_float(key_type) && pass == 0;
-    a.flip_out = is_float(key_type) && pass == plan.places - 1;
-    a.use_bulk = src_aligned ? 1 : 0;
-    a.bin_offsets = offsets + pass * kRadix;
-    a.status = reinterpret_cast<uint32_t*>(w + plan.layout.status_offset[pass & 1]);
-    a.status_clear = pass + 1 < plan.places
-                         ? reinterpret_cast<uint32_t*>(w + plan.layout.status_offset[(pass + 1) & 1])
-                         : nullptr;
-    a.tile_counter = header + kTileCounterWord + pass % 8;
-    a.error = header;
-    a.spin_limit = g_spin_limit;
-    a.fault_tile = g_fault_tile;
-    a.skew_flags = header + kSkewWord + pass;
-    a.digit_xor = pass == plan.places - 1 ? signed_top_xor(key_type, begin_bit, end_bit) : 0u;
-    if (pass >= 8) {
-      // more than 8 passes cannot happen with 8-bit digits of <= 64-bit keys
-      return OS_ERR_INVALID_ARG;
+    for (uint32_t st = 0; st < plan.strips; ++st, ++launch) {
+      const uint64_t lo = (uint64_t)st * plan.strip;
+      PassArgs a{};
+      a.keys_in = static_cast<const char*>(src_k) + lo * kbytes_per_key;
+      a.keys_out = dst_k;
+      a.vals_in = pairs ? src_v + lo : nullptr;
+      a.vals_out = pairs ? dst_v : nullptr;
+      a.n = strip_len(st);
+      a.out_total = (uint32_t)n;
+      a.num_tiles = strip_tiles(st);
+      a.shift = begin_bit + kRadixBits * pass;
+      const int width = end_bit - a.shift < kRadixBits ? end_bit - a.shift : kRadixBits;
+      a.mask = (1u << width) - 1u;
+      a.flip_in = is_float(key_type) && pass == 0;
+      a.flip_out = is_float(key_type) && pass == plan.places - 1;
+      a.use_bulk = src_aligned ? 1 : 0;
+      // strip 0 starts at the global bin offsets; strip st at the bases strip
+      // st-1 left in carry[(st-1) & 1]
+      a.bin_offsets = st == 0 ? offsets + pass * kRadix : carry + ((st - 1) & 1) * kRadix;
+      a.carry_out = st + 1 < plan.strips ? carry + (st & 1) * kRadix : nullptr;
+      a.status = reinterpret_cast<uint32_t*>(w + plan.layout.status_offset[launch & 1]);
+      a.status_clear = launch + 1 < launches
+                           ? reinterpret_cast<uint32_t*>(w + plan.layout.status_offset[(launch + 1) & 1])
+                           : nullptr;
+      a.status_clear_rows = launch + 1 < launches ? strip_tiles((st + 1) % plan.strips) : 0u;
+      if (a.status_clear_rows < a.num_tiles) a.status_clear_rows = a.num_tiles;
+      a.tile_counter = counters + launch;
+      a.error = header;
+      a.spin_limit = g_spin_limit;
+      a.fault_tile = g_fault_tile;
+      a.skew_flags = header + kSkewWord + pass;
+      a.digit_xor = pass == plan.places - 1 ? signed_top_xor(key_type, begin_bit, end_bit) : 0u;
+      if (pass >= 8) {
+        // more than 8 passes cannot happen with 8-bit digits of <= 64-bit keys
+        return OS_ERR_INVALID_ARG;
+      }
+      const int slot = prof_begin(1, pass, s);
+      const cudaError_t e = launch_binning(plan.key_bits, pairs, plan.bucket, a, s);
+      prof_end(slot, s);
+      if (e != cudaSuccess) return OS_ERR_CUDA;
     }
-    const int slot = prof_begin(1, pass, s);
-    const cudaError_t e = launch_binning(plan.key_bits, pairs, plan.bucket, a, s);
-    prof_end(slot, s);
-    if (e != cudaSuccess) return OS_ERR_CUDA;
     src_k = dst_k;
     src_v = dst_v;
     src_aligned = to_out ? aligned_out : true;
@@ -543,6 +593,7 @@ int run_batch(int key_type, const void* keys_in, void* keys_out, const uint32_t*
     a.offsets_stride = (uint32_t)bp.places * kRadix;
     a.status = reinterpret_cast<uint32_t*>(w + bp.status[pass & 1]);
     a.status_clear = pass + 1 < bp.places ? reinterpret_cast<uint32_t*>(w + bp.status[(pass + 1) & 1]) : nullptr;
+    a.status_clear_rows = (uint32_t)bp.max_tiles;  // every tile clears its own row
     a.tile_counter = header + kTileCounterWord + pass % 8;
     a.error = header;
     a.spin_limit = g_spin_limit;
@@ -663,7 +714,7 @@ const char* os_status_string(int status) {
   switch (status) {
     case OS_OK: return "ok";
     case OS_ERR_INVALID_ARG: return "invalid argument";
-    case OS_ERR_TOO_LARGE: return "too many keys (n must be below 2^30)";
+    case OS_ERR_TOO_LARGE: return "too many keys (n must be below 2^32)";
     case OS_ERR_WORKSPACE: return "workspace missing or too small";
     case OS_ERR_CUDA: return "CUDA error";
     case OS_ERR_TIMEOUT: return "chained-scan look-back wait ran past its limit";
@@ -757,6 +808,13 @@ int os_get_tile_config_bucket(int key_bits, int value_bytes, int bucket) {
 void os_debug_set_lookback_fault(int64_t tile, uint32_t spin_limit) {
   g_fault_tile = tile < 0 ? -1 : tile;
   g_spin_limit = spin_limit == 0 ? kDefaultSpinLimit : spin_limit;
+}
+
+uint64_t os_debug_set_strip_keys(uint64_t keys) {
+  if (keys == 0 || keys > kStripKeys) keys = kStripKeys;
+  if (keys < kMinStripKeys) keys = kMinStripKeys;
+  g_strip_keys = keys;
+  return keys;
 }
 
 }  // extern "C"

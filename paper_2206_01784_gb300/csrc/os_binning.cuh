@@ -171,7 +171,8 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
   const uint32_t tile = c.tile, count = c.count;
 
   // the next pass's status counters of this tile start at N
-  if (a.status_clear && tid < kRadix) a.status_clear[(size_t)tile * kRadix + tid] = 0u;
+  if (a.status_clear && tid < kRadix)
+    for (size_t row = tile; row < a.status_clear_rows; row += a.num_tiles) a.status_clear[row * kRadix + tid] = 0u;
   const uint32_t bin_offset = tid < kRadix ? __ldg(c.bin_offsets + tid) : 0u;
   uint32_t* status = a.status + (size_t)tile * kRadix;
   const bool publish = (int64_t)tile != a.fault_tile;
@@ -321,6 +322,8 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
       if (publish) st_relaxed_gpu(status + tid, (kFlagGlobal << kStatusShift) | (exclusive + digit_count));
     }
     gbase[tid] = bin_offset + exclusive - dstart[tid];
+    // the strip's last tile: where the next strip's keys of this digit start
+    if (a.carry_out && tile == a.num_tiles - 1) a.carry_out[tid] = bin_offset + exclusive + digit_count;
   }
   __syncthreads();
 
@@ -403,7 +406,7 @@ __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS, CFG>::NT, BinningC
       c.count = min((uint32_t)T, a.n - c.start);
       c.chain_first = 0;
       c.out_base = 0;
-      c.out_len = a.n;
+      c.out_len = a.out_total;
       c.bin_offsets = a.bin_offsets;
       if (RANK == kRankAdaptive && a.skew_flags) c.skewed = a.skew_flags[0];
     }

@@ -40,11 +40,21 @@ struct PassArgs {
   int use_bulk;              // inputs 16-byte aligned: stage full tiles with bulk copies
   const uint32_t* bin_offsets;  // [256] global bin offsets of this place
   uint32_t* status;          // [num_tiles][256] status counters, zeroed
-  uint32_t* status_clear;    // [num_tiles][256] slab of the next pass, to zero (may be null)
+  uint32_t* status_clear;    // slab of the next launch, to zero (may be null) ...
+  uint32_t status_clear_rows;  // ... rows 0 .. status_clear_rows-1 of it (>= num_tiles)
   uint32_t* tile_counter;    // zeroed; hands out tile ids in launch order
   uint32_t* error;           // device status word
   uint32_t spin_limit;       // look-back polls before giving up
   int64_t fault_tile;        // test hook: tile that never publishes (-1 = none)
+
+  // Strips (Section 3, "Handling very large problems"): a pass over more than
+  // one strip is one launch per strip. keys_in / vals_in point at the strip,
+  // n is the strip's length and bin_offsets hold the strip's bin bases (where
+  // its first key of each digit lands); out_total is the whole array's length
+  // (the output bound). The strip's last tile writes the next strip's bases to
+  // carry_out (null when there is no next strip).
+  uint32_t out_total;
+  uint32_t* carry_out;
 
   // Segmented mode (os_sort_batch); seg_offsets == nullptr means one array of
   // n keys. Each segment is its own sort: its tiles form one look-back chain

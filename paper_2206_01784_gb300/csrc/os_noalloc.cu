@@ -44,7 +44,7 @@ extern "C" OS_API int os_sort_noalloc(int key_type, const void* keys_in, void* k
   const bool pairs = vals_in != nullptr || vals_out != nullptr;
   const size_t need = os_sort_workspace_bytes(key_type, n, pairs ? 4 : 0, begin_bit, end_bit);
   if (need == 0) {
-    // invalid arguments or n >= 2^30: let the regular checks name the error
+    // invalid arguments or n >= 2^32: let the regular checks name the error
     return onesweep::sort_on_workspace(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit,
                                        nullptr, 0, stream);
   }

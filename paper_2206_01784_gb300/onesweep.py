@@ -83,6 +83,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.os_status_string.argtypes = [i32]
     lib.os_debug_set_lookback_fault.restype = None
     lib.os_debug_set_lookback_fault.argtypes = [i64, u32]
+    lib.os_debug_set_strip_keys.restype = u64
+    lib.os_debug_set_strip_keys.argtypes = [u64]
     lib.os_num_tile_configs.restype = i32
     lib.os_num_tile_configs.argtypes = []
     lib.os_tile_config_keys.restype = i32
@@ -180,6 +182,10 @@ def os_status_string(status: int) -> str:
 
 def os_debug_set_lookback_fault(tile: int, spin_limit: int = 0) -> None:
     load().os_debug_set_lookback_fault(tile, spin_limit)
+
+
+def os_debug_set_strip_keys(keys: int) -> int:
+    return int(load().os_debug_set_strip_keys(keys))
 
 
 def os_num_tile_configs() -> int:

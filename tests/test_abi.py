@@ -51,7 +51,8 @@ def test_workspace_sizes():
     assert osw.os_sort_workspace_bytes(7, 100, 0, 0, 32) == 0       # bad key type
     assert osw.os_sort_workspace_bytes(u32, 100, 2, 0, 32) == 0     # bad value width
     assert osw.os_sort_workspace_bytes(u32, 100, 0, 0, 33) == 0     # bad bit range
-    assert osw.os_sort_workspace_bytes(u32, 1 << 30, 0, 0, 32) == 0  # too large
+    assert osw.os_sort_workspace_bytes(u32, 1 << 32, 0, 0, 32) == 0  # too large
+    assert osw.os_sort_workspace_bytes(u32, (1 << 32) - 1, 4, 0, 32) > 8 * ((1 << 32) - 1)  # alternate buffers
     assert osw.os_sort_workspace_bytes(osw.OS_KEY_U64, 100, 0, 0, 64) > 0
 
 
@@ -75,7 +76,7 @@ def test_host_validation_without_gpu():
     u32 = osw.OS_KEY_U32
     fake = 1 << 40  # never dereferenced: every call below fails validation first
     ws_bytes = osw.os_sort_workspace_bytes(u32, 1000, 0, 0, 32)
-    assert osw.os_sort_keys(u32, fake, fake + 8192, 1 << 30, 0, 32, fake + 65536, 1 << 40, 0) == osw.OS_ERR_TOO_LARGE
+    assert osw.os_sort_keys(u32, fake, fake + 8192, 1 << 32, 0, 32, fake + 65536, 1 << 40, 0) == osw.OS_ERR_TOO_LARGE
     assert osw.os_sort_keys(u32, fake, fake + 8192, 1000, 0, 40, fake + 65536, ws_bytes, 0) == osw.OS_ERR_INVALID_ARG
     assert osw.os_sort_keys(u32, fake, fake + 8192, 1000, 9, 8, fake + 65536, ws_bytes, 0) == osw.OS_ERR_INVALID_ARG
     assert osw.os_sort_keys(9, fake, fake + 8192, 1000, 0, 32, fake + 65536, ws_bytes, 0) == osw.OS_ERR_INVALID_ARG
@@ -95,7 +96,7 @@ def test_host_validation_without_gpu():
 def test_status_strings():
     for s in range(6):
         assert osw.os_status_string(s)
-    assert "2^30" in osw.os_status_string(osw.OS_ERR_TOO_LARGE)
+    assert "2^32" in osw.os_status_string(osw.OS_ERR_TOO_LARGE)
 
 
 def test_tile_configs_host_side():
