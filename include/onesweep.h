@@ -36,7 +36,7 @@
  *    their keys.
  *  - n must be below 2^32 (output positions are 32-bit); larger n returns
  *    OS_ERR_TOO_LARGE. The chained scan keeps 30-bit counts, so passes over
- *    more than 2^28 keys run strip by strip (Section 3, "Handling very large
+ *    2^30 keys or more run strip by strip (Section 3, "Handling very large
  *    problems"; see os_debug_set_strip_keys).
  *  - Inputs are never modified. Input, output and workspace ranges must not
  *    overlap (OS_ERR_INVALID_ARG). Key pointers must be aligned to the key
@@ -243,11 +243,11 @@ OS_API void os_debug_set_lookback_fault(int64_t tile, uint32_t spin_limit);
  * Strip length of single-array sorts (Section 3, "Handling very large
  * problems"): a pass over more keys than one strip runs as one binning launch
  * per strip, each strip a chain of its own, the next strip's bins starting
- * where the previous strip's ended. The default, 2^28 keys (rounded down to a
- * whole number of tiles), keeps every look-back count below the 30-bit limit;
- * tests set shorter strips to run the multi-strip path on small inputs.
- * `keys` is clamped to [2^16, 2^28]; 0 restores the default. Returns the
- * value set. Process-wide, applied when a sort is planned; a workspace sized
+ * where the previous strip's ended. Strips are at most 2^30 - 1 keys (every
+ * look-back count stays below the 30-bit limit) and of equal length in whole
+ * tiles; this sets that maximum, so tests can run the multi-strip path on
+ * small inputs. `keys` is clamped to [2^16, 2^30 - 1]; 0 restores the
+ * default. Returns the value set. Process-wide, applied when a sort is planned; a workspace sized
  * for n fits any strip length.
  */
 OS_API uint64_t os_debug_set_strip_keys(uint64_t keys);

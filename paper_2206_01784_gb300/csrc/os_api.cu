@@ -102,7 +102,7 @@ namespace {
 // launch each, every strip its own look-back chain); 32-bit output indices
 // then bound n below 2^32.
 constexpr uint64_t kMaxKeys = 1ull << 32;
-constexpr uint64_t kStripKeys = 1ull << 28;
+constexpr uint64_t kStripKeys = (1ull << 30) - 1;  // every count of a strip fits 30 bits
 constexpr uint64_t kMinStripKeys = 1ull << 16;
 uint64_t g_strip_keys = kStripKeys;  // shorter strips: os_debug_set_strip_keys
 constexpr size_t kAlign = 256;
@@ -199,8 +199,12 @@ int make_plan(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_
   plan->bucket = size_bucket(n);
   plan->tile = binning_tile_keys(kb, plan->pairs, plan->bucket);
   plan->tiles = (uint32_t)((n + plan->tile - 1) / plan->tile);
-  uint64_t strip = g_strip_keys / plan->tile * plan->tile;
-  if (strip == 0) strip = plan->tile;
+  // strips of equal length (whole tiles, at most the strip limit), so that no
+  // launch is much shorter than the next one, whose status rows it clears
+  const uint64_t max_strip = g_strip_keys / plan->tile * plan->tile;
+  const uint64_t want = n == 0 ? 1u : (n + max_strip - 1) / max_strip;
+  uint64_t strip = (n + want - 1) / want;
+  strip = (strip + plan->tile - 1) / plan->tile * plan->tile;
   plan->strip = strip;
   plan->strips = n == 0 ? 1u : (uint32_t)((n + strip - 1) / strip);
   // status slabs: rows for the largest launch (at most one strip of the
@@ -210,7 +214,8 @@ int make_plan(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_
   const uint64_t max_tiles = (launch_keys + min_tile - 1) / min_tile;
   // one tile counter per launch: 8 places x strips, for any strip length the
   // test hook allows (>= kMinStripKeys rounded down to a tile of < 2^15 keys,
-  // so longer than 2^15 keys; a workspace sized once always fits)
+  // then balanced: longer than n / (n / 2^15 + 1) keys; a workspace sized
+  // once always fits)
   const uint64_t max_strips = n / (kMinStripKeys / 2) + 2;
   os_workspace_layout& L = plan->layout;
   std::memset(&L, 0, sizeof(L));

@@ -148,6 +148,51 @@ __device__ __forceinline__ uint32_t wlms_rank(uint32_t* msk, uint32_t* cnt, uint
   return old + below;
 }
 
+// Decoupled look-back of one digit (step 6b) in rounds: issue() reads the
+// counters of up to W preceding tiles (one L2 round trip), consume() folds in
+// what came back - stopping at a counter not yet published, which the next
+// round reads again - until a G counter or the chain's first tile is reached,
+// and then publishes this tile's (G, inclusive prefix).
+template <int W>
+struct Lookback {
+  uint32_t s[W];       // counters of the round in flight
+  uint32_t left;       // preceding tiles of the chain not yet accumulated
+  uint32_t exclusive;  // sum of the accumulated counters
+  uint32_t own;        // this tile's count of the digit
+  uint32_t* mine;      // this tile's counter of the digit (null: publish nothing)
+  bool done;
+
+  __device__ __forceinline__ void start(uint32_t tile, uint32_t chain_first) {
+    left = tile - chain_first;
+    exclusive = 0u;
+    done = left == 0u;
+  }
+  // (G, exclusive + own): the inclusive prefix of the digit through this tile
+  __device__ __forceinline__ void publish_global() {
+    if (mine) st_relaxed_gpu(mine, (kFlagGlobal << kStatusShift) | (exclusive + own));
+  }
+  // reads tiles chain_first + left - 1, chain_first + left - 2, ...
+  __device__ __forceinline__ void issue(const uint32_t* status, uint32_t chain_first, int digit) {
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+      s[w] = (uint32_t)w < left ? ld_relaxed_gpu(status + (size_t)(chain_first + left - 1u - w) * kRadix + digit)
+                                : (kFlagGlobal << kStatusShift);
+  }
+  __device__ __forceinline__ void consume() {
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      if (done) break;
+      const uint32_t flag = s[w] >> kStatusShift;
+      if (flag == kFlagNotReady) break;  // read this tile again next round
+      exclusive += s[w] & kValueMask;
+      --left;
+      if (flag == kFlagGlobal || left == 0u) done = true;
+    }
+    if (done) publish_global();
+  }
+};
+constexpr int kLookbackWindow = 4;
+
 template <int KBITS, bool PAIRS, int CFG, int RANK, int FLIP, bool FULL>
 __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* smem, const TileCtx& c) {
   using C = BinningConfig<KBITS, PAIRS, CFG>;
@@ -287,40 +332,33 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
     }
   }
 
-  // 6b. decoupled look-back for digit tid over the preceding tiles of the
-  //     chain; the counters of up to kWindow predecessors are read per round
-  //     trip
-  if (tid < kRadix) {
-    uint32_t exclusive = 0;
-    if (!chain_head) {
-      constexpr int kWindow = 4;
-      const int64_t lo = c.chain_first;
-      int64_t k = (int64_t)tile - 1;  // nearest tile not yet accumulated
-      uint32_t spins = 0;
-      bool done = false;
-      while (!done) {
-        uint32_t s[kWindow];
-#pragma unroll
-        for (int w = 0; w < kWindow; ++w)
-          s[w] = k - w >= lo ? ld_relaxed_gpu(a.status + (size_t)(k - w) * kRadix + tid)
-                             : (kFlagGlobal << kStatusShift);
-#pragma unroll
-        for (int w = 0; w < kWindow && !done; ++w) {
-          const uint32_t flag = s[w] >> kStatusShift;
-          if (flag == kFlagNotReady) break;  // re-read from tile k next round
-          exclusive += s[w] & kValueMask;
-          --k;
-          if (flag == kFlagGlobal || k < lo) done = true;
-        }
-        if (done) break;
-        if (++spins >= a.spin_limit) {
-          atomicOr(a.error, kErrTimeout);
-          break;
-        }
-        if ((spins & 255u) == 0 && (ld_relaxed_gpu(a.error) & kErrTimeout)) break;
+  // 6b. decoupled look-back: thread d walks back over the counters of digit
+  //     d in the preceding tiles of the chain, up to kLookbackWindow per round
+  //     trip, until it reaches a G counter; then it publishes (G, inclusive
+  //     prefix) for this tile
+  uint32_t exclusive = 0;
+  if (tid < kRadix && !chain_head) {
+    Lookback<kLookbackWindow> lb;
+    lb.start(tile, c.chain_first);
+    lb.mine = publish ? status + tid : nullptr;
+    lb.own = digit_count;
+    uint32_t spins = 0;
+    while (!lb.done) {
+      lb.issue(a.status, c.chain_first, tid);
+      lb.consume();  // publishes G when the walk ends
+      if (lb.done) break;
+      if (++spins >= a.spin_limit) {
+        atomicOr(a.error, kErrTimeout);
+        break;
       }
-      if (publish) st_relaxed_gpu(status + tid, (kFlagGlobal << kStatusShift) | (exclusive + digit_count));
+      if ((spins & 255u) == 0 && (ld_relaxed_gpu(a.error) & kErrTimeout)) break;
     }
+    // a wait that gave up still publishes (the error is recorded; the
+    // successors' walks then end instead of timing out one after another)
+    if (!lb.done) lb.publish_global();
+    exclusive = lb.exclusive;
+  }
+  if (tid < kRadix) {
     gbase[tid] = bin_offset + exclusive - dstart[tid];
     // the strip's last tile: where the next strip's keys of this digit start
     if (a.carry_out && tile == a.num_tiles - 1) a.carry_out[tid] = bin_offset + exclusive + digit_count;
@@ -398,7 +436,7 @@ __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS, CFG>::NT, BinningC
           c.out_base = (uint32_t)s0;
           c.out_len = len;
           c.bin_offsets = a.bin_offsets + (size_t)seg * a.offsets_stride;
-        if (RANK == kRankAdaptive && a.skew_flags) c.skewed = a.skew_flags[(size_t)seg * a.skew_stride];
+          if (RANK == kRankAdaptive && a.skew_flags) c.skewed = a.skew_flags[(size_t)seg * a.skew_stride];
         }
       }
     } else if (tile < a.num_tiles) {

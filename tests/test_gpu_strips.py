@@ -1,12 +1,12 @@
-"""Strips (Section 3, "Handling very large problems"): passes longer than one
-strip run as one chained scan per strip, each strip's bins starting where
-the previous strip's ended.
+"""Strips (Section 3, "Handling very large problems"): passes over 2^30 keys
+or more run as one chained scan per strip (strips of equal length, each below
+2^30 keys), each strip's bins starting where the previous strip's ended.
 
-The default strip is 2^28 keys, so the multi-strip path is exercised here on
-small inputs with the shortest strip the library allows (2^16 keys rounded
-down to whole tiles), bit-exact against the oracle; the slow cases run it at
-its real length: 2^28 + 2^20 + 12345 uint32 pairs against the oracle, and
-2^30 + 12345 uint32 pairs by the properties that pin the stable sort.
+The multi-strip path is exercised here on small inputs with the shortest
+strip limit the library allows (2^16 keys), bit-exact against the oracle; the
+slow cases run 2^28 + 12345 uint32 pairs in 2^26-key strips against the
+oracle, and 2^30 + 12345 uint32 pairs (two strips at the default limit) by
+the properties that pin the stable sort.
 """
 import numpy as np
 import pytest
@@ -48,7 +48,8 @@ def short_strips():
 
 
 def _strip_len(kt, pairs, n_hint=4 * SHORT):
-    # the tile of a sort of about n_hint keys (the geometry depends on size)
+    # the strip limit in whole tiles of a sort of about n_hint keys (the
+    # geometry depends on size); the library then balances the strips
     tile = osw.os_sort_workspace_layout(osw.KEY_TYPES[kt], n_hint, 4 if pairs else 0, 0, KB[kt]).tile_keys
     return SHORT // tile * tile
 
@@ -98,7 +99,8 @@ def test_short_strips_bit_ranges(short_strips, kt, begin, end):
 
 
 def test_short_strips_boundaries(short_strips):
-    # exactly one strip, one key past it, exact multiple of the strip
+    # exactly the strip limit, one key past it (two half strips), an exact
+    # multiple of it, one key short of two
     strip = _strip_len("u32", True)
     for n in (strip, strip + 1, 3 * strip, 2 * strip - 1):
         keys = _keys("u32", "and2", n, seed=n)
@@ -145,19 +147,23 @@ def test_workspace_sized_once_fits_short_strips():
 
 
 @pytest.mark.slow
-def test_two_default_strips_exact():
+def test_large_strips_exact():
     _dev()
-    n = (1 << 28) + (1 << 20) + 12345
+    n = (1 << 28) + 12345  # five strips of 2^26 keys or less
     keys = workload.keys("u32", "uniform", n, 11)
     vals = workload.iota_u32(n)
-    got = _sort("u32", keys, vals, 0, 32)
+    osw.os_debug_set_strip_keys(1 << 26)
+    try:
+        got = _sort("u32", keys, vals, 0, 32)
+    finally:
+        osw.os_debug_set_strip_keys(0)
     exp = oracle.sort("u32", keys, vals, 0, 32)
     assert np.array_equal(got[0], exp[0]) and np.array_equal(got[1], exp[1])
 
 
 @pytest.mark.slow
 def test_beyond_2_30_keys_by_properties():
-    # n past the 30-bit count limit of one chained scan: five strips per pass.
+    # n past the 30-bit count limit of one chained scan: two strips per pass.
     # Properties that hold exactly for the stable sort, checked on the host.
     _dev()
     n = (1 << 30) + 12345
