@@ -46,6 +46,7 @@ def parse_args():
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--e2e-lanes", type=int, default=3, help="streams (each with a device workspace) the end-to-end calls rotate over")
     p.add_argument("--keys-only", action="store_true", help="sort keys without values")
     p.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
     p.add_argument("--serve-requests", type=int, default=10000)
@@ -406,77 +407,67 @@ def main():
                      "histogram_avg_ms": statistics.mean(hist_ms) if hist_ms else None,
                      "binning_avg_ms": bin_avg}
 
-    # End to end through the C ABI: every step uploads its keys (and values)
-    # from pinned host memory, sorts, and downloads the sorted result. Steps
-    # are pipelined the way a stream of arrays would be served: uploads, sorts
-    # and downloads run on three streams over two device buffer sets, so step
-    # i's sort overlaps step i+1's upload and step i-1's download.
+    # End to end through the C ABI's host-buffer entry point: every step's
+    # call uploads its keys (and values) from pinned host memory, sorts them
+    # and downloads the sorted result into pinned host memory. Calls rotate
+    # over three streams with a device workspace each, so one array's upload,
+    # another's sort and a third's download overlap, the way a stream of
+    # arrays would be served.
     e2e = None
     if args.e2e_steps > 0:
         hk = torch.from_numpy(keys_np.view(np.int32)).pin_memory()
         hv = torch.from_numpy(vals_np.view(np.int32)).pin_memory()
-        hko = torch.empty_like(hk).pin_memory()
-        hvo = torch.empty_like(hv).pin_memory()
-        sets = [(keys, vals, keys_out, vals_out, ws)]
-        sets.append((torch.empty_like(keys), torch.empty_like(vals), torch.empty_like(keys_out),
-                     torch.empty_like(vals_out), torch.empty_like(ws)))
-        up_s, sort_s, down_s = (torch.cuda.Stream(dev) for _ in range(3))
-        ev = lambda: torch.cuda.Event()  # noqa: E731
-        uploaded, sorted_, downloaded = [ev(), ev()], [ev(), ev()], [ev(), ev()]
-        for e in sorted_ + downloaded:
-            e.record(torch.cuda.current_stream(dev))
-        barrier()
+        lanes = max(1, args.e2e_lanes)
+        hko = [torch.empty_like(hk).pin_memory() for _ in range(lanes)]
+        hvo = [torch.empty_like(hv).pin_memory() for _ in range(lanes)]
+        hws = osw.os_sort_host_workspace_bytes(kt, n, 4 if pairs else 0, 0, 32)
+        wss = [torch.empty(hws, dtype=torch.uint8, device=dev) for _ in range(lanes)]
+        streams = [torch.cuda.Stream(dev) for _ in range(lanes)]
 
         def e2e_step(i):
-            b = i % 2
-            k, v, ko, vo, w = sets[b]
-            with torch.cuda.stream(up_s):
-                up_s.wait_event(sorted_[b])  # the sort two steps back has read this input set
-                k.copy_(hk, non_blocking=True)
-                if pairs:
-                    v.copy_(hv, non_blocking=True)
-                uploaded[b].record(up_s)
-            sort_s.wait_event(uploaded[b])
-            sort_s.wait_event(downloaded[b])  # this output set was downloaded
+            b = i % lanes
+            sp_b = streams[b].cuda_stream
             if pairs:
-                rc = osw.os_sort_pairs(kt, k.data_ptr(), ko.data_ptr(), v.data_ptr(), vo.data_ptr(), n, 0, 32,
-                                       w.data_ptr(), w.numel(), sort_s.cuda_stream)
+                rc = osw.os_sort_pairs_host(kt, hk.data_ptr(), hko[b].data_ptr(), hv.data_ptr(), hvo[b].data_ptr(),
+                                            n, 0, 32, wss[b].data_ptr(), hws, sp_b)
             else:
-                rc = osw.os_sort_keys(kt, k.data_ptr(), ko.data_ptr(), n, 0, 32, w.data_ptr(), w.numel(),
-                                      sort_s.cuda_stream)
+                rc = osw.os_sort_keys_host(kt, hk.data_ptr(), hko[b].data_ptr(), n, 0, 32, wss[b].data_ptr(), hws,
+                                           sp_b)
             if rc != osw.OS_OK:
-                raise osw.OnesweepError(rc, "sort")
-            sorted_[b].record(sort_s)
-            with torch.cuda.stream(down_s):
-                down_s.wait_event(sorted_[b])
-                hko.copy_(ko, non_blocking=True)
-                if pairs:
-                    hvo.copy_(vo, non_blocking=True)
-                downloaded[b].record(down_s)
+                raise osw.OnesweepError(rc, "sort (host buffers)")
 
-        for i in range(2):
+        for i in range(lanes):
             e2e_step(i)
         torch.cuda.synchronize(dev)
         barrier()
+        e0 = [torch.cuda.Event(enable_timing=True) for _ in range(lanes)]
+        e1 = [torch.cuda.Event(enable_timing=True) for _ in range(lanes)]
         t0 = time.perf_counter()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e0.record(up_s)
+        for b in range(lanes):
+            e0[b].record(streams[b])
         for i in range(args.e2e_steps):
             e2e_step(i)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e1.record(down_s)
+        for b in range(lanes):
+            e1[b].record(streams[b])
         torch.cuda.synchronize(dev)
         barrier()
-        et_ms = max(e0.elapsed_time(e1), 0.0)
         wall_ms = (time.perf_counter() - t0) * 1e3
+        et_ms = max(max(e0[a].elapsed_time(e1[b]) for a in range(lanes) for b in range(lanes)), 0.0)
         et = torch.tensor([max(et_ms, wall_ms)], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(et, op=dist.ReduceOp.MAX)
+        for b in range(lanes):
+            st = osw.os_workspace_status(wss[b].data_ptr(), streams[b].cuda_stream)
+            if st != osw.OS_OK:
+                raise osw.OnesweepError(st, "device status after the end-to-end steps")
         e2e = {"value": world * n * args.e2e_steps / (float(et.item()) / 1e3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": hk.numel() * 4 + (hv.numel() * 4 if pairs else 0),
-               "d2h_bytes_per_step": hko.numel() * 4 + (hvo.numel() * 4 if pairs else 0), "steps": args.e2e_steps,
-               "pipelined": "uploads, sorts and downloads on three streams, two device buffer sets"}
-        ok = np.array_equal(hko.numpy().view(np.uint32)[:: 1 << 16], keys_out.cpu().numpy().view(np.uint32)[:: 1 << 16])
+               "d2h_bytes_per_step": hk.numel() * 4 + (hv.numel() * 4 if pairs else 0), "steps": args.e2e_steps,
+               "api": "os_sort_pairs_host" if pairs else "os_sort_keys_host",
+               "pipelined": f"calls rotate over {lanes} streams with a device workspace each"}
+        last = (args.e2e_steps - 1) % lanes
+        ok = np.array_equal(hko[last].numpy().view(np.uint32)[:: 1 << 16],
+                            keys_out.cpu().numpy().view(np.uint32)[:: 1 << 16])
         if not ok:
             raise RuntimeError("end-to-end result differs from the device result")
 

@@ -125,6 +125,30 @@ OS_API int os_sort_pairs(int key_type, const void *keys_in, void *keys_out, cons
                   uint64_t n, int begin_bit, int end_bit, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * The same sorts for arrays held in HOST memory. keys_in / vals_in: n keys
+ * (uint32 values) in host memory, read; keys_out / vals_out: n keys (values)
+ * in host memory, written with the stable ascending order. The call enqueues
+ * on `stream`, in order, the uploads into staging buffers inside ws, the
+ * sort (os_sort_keys / os_sort_pairs on those buffers) and the downloads; the
+ * output is complete when the stream gets past the call (cudaStreamSynchronize,
+ * or os_workspace_status(ws, stream)). Host buffers should be page-locked
+ * (cudaHostAlloc / cudaHostRegister) for the copies to run asynchronously;
+ * pageable buffers work, but the call then waits for its copies. ws:
+ * os_sort_host_workspace_bytes() bytes of DEVICE memory (16-byte aligned);
+ * it begins with the sort's own workspace, so os_workspace_status(ws, ...)
+ * reports device-side errors as for os_sort_keys. Host ranges must not
+ * overlap (OS_ERR_INVALID_ARG). Not part of the paper: the sort as a caller
+ * with data in host memory uses it (two calls on two streams with two
+ * workspaces overlap one array's copies with another's sort).
+ */
+OS_API size_t os_sort_host_workspace_bytes(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_bit);
+OS_API int os_sort_keys_host(int key_type, const void *keys_in, void *keys_out, uint64_t n, int begin_bit,
+                             int end_bit, void *ws, size_t ws_bytes, void *stream);
+OS_API int os_sort_pairs_host(int key_type, const void *keys_in, void *keys_out, const uint32_t *vals_in,
+                              uint32_t *vals_out, uint64_t n, int begin_bit, int end_bit, void *ws, size_t ws_bytes,
+                              void *stream);
+
+/*
  * Segmented (batched) sort: num_segments independent arrays held back to
  * back, segment s = [seg_offsets[s], seg_offsets[s+1]), each sorted on its
  * own, in one call of a few launches whatever the number of segments (each

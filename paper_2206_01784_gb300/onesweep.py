@@ -85,6 +85,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.os_debug_set_lookback_fault.argtypes = [i64, u32]
     lib.os_debug_set_strip_keys.restype = u64
     lib.os_debug_set_strip_keys.argtypes = [u64]
+    lib.os_sort_host_workspace_bytes.restype = sz
+    lib.os_sort_host_workspace_bytes.argtypes = [i32, u64, i32, i32, i32]
+    lib.os_sort_keys_host.restype = i32
+    lib.os_sort_keys_host.argtypes = [i32, vp, vp, u64, i32, i32, vp, sz, vp]
+    lib.os_sort_pairs_host.restype = i32
+    lib.os_sort_pairs_host.argtypes = [i32, vp, vp, vp, vp, u64, i32, i32, vp, sz, vp]
     lib.os_num_tile_configs.restype = i32
     lib.os_num_tile_configs.argtypes = []
     lib.os_tile_config_keys.restype = i32
@@ -186,6 +192,20 @@ def os_debug_set_lookback_fault(tile: int, spin_limit: int = 0) -> None:
 
 def os_debug_set_strip_keys(keys: int) -> int:
     return int(load().os_debug_set_strip_keys(keys))
+
+
+def os_sort_host_workspace_bytes(key_type: int, n: int, value_bytes: int, begin_bit: int, end_bit: int) -> int:
+    return int(load().os_sort_host_workspace_bytes(key_type, n, value_bytes, begin_bit, end_bit))
+
+
+def os_sort_keys_host(key_type, keys_in, keys_out, n, begin_bit, end_bit, ws, ws_bytes, stream) -> int:
+    return int(load().os_sort_keys_host(key_type, keys_in, keys_out, n, begin_bit, end_bit, ws, ws_bytes, stream))
+
+
+def os_sort_pairs_host(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws, ws_bytes,
+                       stream) -> int:
+    return int(load().os_sort_pairs_host(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws,
+                                         ws_bytes, stream))
 
 
 def os_num_tile_configs() -> int:

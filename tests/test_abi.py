@@ -164,3 +164,25 @@ def test_size_buckets_and_tuning_table_roundtrip(tmp_path):
         assert osw.os_get_tile_config_bucket(32, 4, -1) == -1
     finally:
         autotune.apply(saved)
+
+
+def test_host_api_validation_without_gpu():
+    u32 = osw.OS_KEY_U32
+    n = 1000
+    dev_ws = osw.os_sort_workspace_bytes(u32, n, 4, 0, 32)
+    host_ws = osw.os_sort_host_workspace_bytes(u32, n, 4, 0, 32)
+    assert host_ws >= dev_ws + 4 * n * 4
+    assert osw.os_sort_host_workspace_bytes(u32, n, 0, 0, 32) < host_ws
+    assert osw.os_sort_host_workspace_bytes(9, n, 0, 0, 32) == 0
+    assert osw.os_sort_host_workspace_bytes(u32, 1 << 32, 0, 0, 32) == 0
+    fake = 1 << 40  # never dereferenced: every call below fails validation first
+    hk, hko, hv, hvo, ws = fake, fake + 8192, fake + 16384, fake + 24576, fake + (1 << 20)
+    assert osw.os_sort_pairs_host(u32, hk, hko, hv, hvo, 1 << 32, 0, 32, ws, 1 << 40, 0) == osw.OS_ERR_TOO_LARGE
+    assert osw.os_sort_pairs_host(9, hk, hko, hv, hvo, n, 0, 32, ws, host_ws, 0) == osw.OS_ERR_INVALID_ARG
+    assert osw.os_sort_pairs_host(u32, hk, hko, None, hvo, n, 0, 32, ws, host_ws, 0) == osw.OS_ERR_INVALID_ARG
+    assert osw.os_sort_pairs_host(u32, hk, hk + 400, hv, hvo, n, 0, 32, ws, host_ws, 0) == osw.OS_ERR_INVALID_ARG
+    assert osw.os_sort_pairs_host(u32, hk, hko, hv, hko + 40, n, 0, 32, ws, host_ws, 0) == osw.OS_ERR_INVALID_ARG
+    assert osw.os_sort_pairs_host(u32, hk, hko, hv, hvo, n, 0, 32, ws, host_ws - 1, 0) == osw.OS_ERR_WORKSPACE
+    assert osw.os_sort_pairs_host(u32, hk, hko, hv, hvo, n, 0, 32, None, host_ws, 0) == osw.OS_ERR_WORKSPACE
+    assert osw.os_sort_pairs_host(u32, hk, hko, hv, hvo, n, 0, 32, ws + 8, host_ws, 0) == osw.OS_ERR_INVALID_ARG
+    assert osw.os_sort_keys_host(u32, None, None, 0, 0, 32, None, 0, 0) == osw.OS_OK
