@@ -46,6 +46,8 @@ def parse_args():
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--serve-sweep", default="0.5,0.9",
+                   help="other offered loads (fractions of the measured capacity) for the serving stream")
     p.add_argument("--e2e-lanes", type=int, default=3, help="streams (each with a device workspace) the end-to-end calls rotate over")
     p.add_argument("--keys-only", action="store_true", help="sort keys without values")
     p.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
@@ -275,7 +277,7 @@ def measure_batch(torch, osw, workload, np, dev, steps: int = 20):
             "identical_output": identical, "tile_variant": osw.os_get_tile_config_bucket(32, 4, osw.os_size_bucket(n // len(sizes)))}
 
 
-def measure_serving(torch, dev, count: int):
+def measure_serving(torch, dev, count: int, sweep_loads=()):
     """Continuous batching of a Poisson request stream (sizes log-uniform
     16K-64M keys, key types 60/25/15 % u32/u64/f32 with u32 values, 40 GB
     device budget, seed 11): capacity first (every request present at once),
@@ -292,13 +294,19 @@ def measure_serving(torch, dev, count: int):
     capacity_rps = cap["gkeys_per_s"] * 1e9 / mean_keys
     reqs = serve.make_requests(count, seed=11, rate_per_s=0.7 * capacity_rps)
     st = srv.run(reqs, realtime=True)
+    # the same stream offered at other fractions of the capacity
+    sweep = []
+    for load in sweep_loads:
+        sw = srv.run(serve.make_requests(count, seed=11, rate_per_s=load * capacity_rps), realtime=True)
+        sweep.append({"load": load, "gkeys_per_s": sw["gkeys_per_s"], "p50_ms": sw["p50_ms"], "p99_ms": sw["p99_ms"],
+                      "mean_batch_requests": sw["mean_batch_requests"]})
     return {"workload": f"{count} requests, Poisson arrivals at 0.7x measured capacity, sizes log-uniform 16K-64M, "
                         "u32/u64/f32 keys 60/25/15 % + u32 values, 40 GB budget, inputs copied from pinned host "
                         "memory, seed 11",
             "capacity_gkeys_per_s": cap["gkeys_per_s"], "offered_requests_per_s": 0.7 * capacity_rps,
             "gkeys_per_s": st["gkeys_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "mean_ms": st["mean_ms"], "batches": st["batches"], "mean_batch_requests": st["mean_batch_requests"],
-            "keys": st["keys"]}
+            "keys": st["keys"], "load_sweep": sweep}
 
 
 def main():
@@ -479,7 +487,8 @@ def main():
     if world == 1 and not args.no_extras:
         batched = measure_batch(torch, osw, workload, np, dev)
         if args.serve_requests > 0:
-            serving = measure_serving(torch, dev, args.serve_requests)
+            loads = [float(x) for x in args.serve_sweep.split(",") if x.strip()]
+            serving = measure_serving(torch, dev, args.serve_requests, loads)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
