@@ -41,7 +41,9 @@ def parse_args():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--log2n", type=int, default=28, help="keys per GPU = 2^log2n")
+    p.add_argument("--log2n", type=int, default=None,
+                   help="keys per GPU = 2^log2n (default 28; 27 for 64-bit keys, the u64 configuration)")
+    p.add_argument("--key-type", choices=["u32", "u64", "f32", "f64", "i32", "i64"], default="u32")
     p.add_argument("--dist", default="uniform")
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -52,13 +54,37 @@ def parse_args():
     p.add_argument("--keys-only", action="store_true", help="sort keys without values")
     p.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
     p.add_argument("--serve-requests", type=int, default=10000)
-    return p.parse_args()
+    args = p.parse_args()
+    if args.log2n is None:
+        args.log2n = 27 if args.key_type in ("u64", "f64", "i64") else 28
+    if args.key_type in ("f32", "f64") and args.dist == "uniform":
+        args.dist = "normal"  # the float workload: N(0,1) with signed zeros and duplicates
+    return args
 
 
-def workload_name(n, dist, seed, pairs=True):
+KEY_BITS = {"u32": 32, "u64": 64, "f32": 32, "f64": 64, "i32": 32, "i64": 64}
+
+
+def order_key(torch, t, key_type):
+    """int64 tensor whose signed order is the sort order of key_type's bits
+    (t: int32 or int64 tensor holding the bits), for the sanity check."""
+    if key_type in ("u32", "i32", "f32"):
+        x = t.to(torch.int32)
+        if key_type == "f32":  # sign-flip: negative floats all bits inverted, others sign bit set
+            x = x ^ ((x >> 31) | torch.tensor(-(1 << 31), dtype=torch.int32, device=t.device))
+        x64 = x.to(torch.int64)
+        return x64 if key_type == "i32" else x64 & 0xFFFFFFFF
+    x = t.to(torch.int64)
+    smin = torch.tensor(-(1 << 63), dtype=torch.int64, device=t.device)
+    if key_type == "f64":
+        x = x ^ ((x >> 63) | smin)
+    return x if key_type == "i64" else x ^ smin
+
+
+def workload_name(n, dist, seed, pairs=True, key_type="u32"):
     size = f"{n >> 20}M" if n >= (1 << 20) else str(n)
     payload = " + u32 index values" if pairs else " only"
-    return f"{size} u32 keys{payload}, {dist} keys (seed {seed})"
+    return f"{size} {key_type} keys{payload}, {dist} keys (seed {seed})"
 
 
 # The sources the timed binning kernel is compiled from: a profile's traffic
@@ -171,17 +197,17 @@ def cpu_model() -> str:
     return "unknown"
 
 
-def time_oracle(n: int, dist: str, seed: int, repeats: int = 1):
+def time_oracle(n: int, dist: str, seed: int, repeats: int = 1, key_type: str = "u32"):
     """The CPU oracle as it stands (single thread), on n pairs of the workload."""
     import oracle
     from paper_2206_01784_gb300 import workload
 
-    keys = workload.keys("u32", dist, n, seed)
+    keys = workload.keys(key_type, dist, n, seed)
     vals = workload.iota_u32(n)
     times = []
     for _ in range(repeats):
         t0 = time.perf_counter()
-        oracle.sort("u32", keys, vals)
+        oracle.sort(key_type, keys, vals)
         times.append(time.perf_counter() - t0)
     return times
 
@@ -196,17 +222,17 @@ def run_reference(args):
     n = 1 << 22
     while n > (1 << 16) and n * (args.steps + args.warmup) > 840_000_000:
         n >>= 1
-    times = time_oracle(n, args.dist, args.seed, repeats=args.warmup + args.steps)[args.warmup:]
+    times = time_oracle(n, args.dist, args.seed, repeats=args.warmup + args.steps, key_type=args.key_type)[args.warmup:]
     total = sum(times)
     value = n * len(times) / total / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total / len(times) * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic", "impl": "reference",
-        "config": {"workload": workload_name(1 << args.log2n, args.dist, args.seed),
+        "scaling": "weak", "vs_baseline": None, "dtype": args.key_type, "data": "synthetic", "impl": "reference",
+        "config": {"workload": workload_name(1 << args.log2n, args.dist, args.seed, key_type=args.key_type),
                    "sample_keys_per_step": n},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{n} u32 pairs of the same distribution per step, single-threaded C oracle",
+                         "sample": f"{n} {args.key_type} pairs of the same distribution per step, single-threaded C oracle",
                          "cpu": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -337,15 +363,18 @@ def main():
     osw.load()
     n = 1 << args.log2n
     seed = args.seed + 1000 * rank
-    keys_np = workload.keys("u32", args.dist, n, seed)
+    bits = KEY_BITS[args.key_type]
+    kbytes = bits // 8
+    kview = np.int64 if bits == 64 else np.int32
+    keys_np = workload.keys(args.key_type, args.dist, n, seed)
     vals_np = workload.iota_u32(n)
-    keys = torch.from_numpy(keys_np.view(np.int32)).to(dev)
+    keys = torch.from_numpy(keys_np.view(kview)).to(dev)
     vals = torch.from_numpy(vals_np.view(np.int32)).to(dev)
     keys_out = torch.empty_like(keys)
     vals_out = torch.empty_like(vals)
-    kt = osw.OS_KEY_U32
+    kt = osw.KEY_TYPES[args.key_type]
     pairs = not args.keys_only
-    lay = osw.os_sort_workspace_layout(kt, n, 4 if pairs else 0, 0, 32)
+    lay = osw.os_sort_workspace_layout(kt, n, 4 if pairs else 0, 0, bits)
     ws = torch.empty(lay.total_bytes, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
@@ -353,9 +382,9 @@ def main():
     def step():
         if pairs:
             rc = osw.os_sort_pairs(kt, keys.data_ptr(), keys_out.data_ptr(), vals.data_ptr(), vals_out.data_ptr(), n,
-                                   0, 32, ws.data_ptr(), ws.numel(), sp)
+                                   0, bits, ws.data_ptr(), ws.numel(), sp)
         else:
-            rc = osw.os_sort_keys(kt, keys.data_ptr(), keys_out.data_ptr(), n, 0, 32, ws.data_ptr(), ws.numel(), sp)
+            rc = osw.os_sort_keys(kt, keys.data_ptr(), keys_out.data_ptr(), n, 0, bits, ws.data_ptr(), ws.numel(), sp)
         if rc != osw.OS_OK:
             raise osw.OnesweepError(rc, "os_sort_pairs")
 
@@ -392,7 +421,7 @@ def main():
     value = world * n * args.steps / (max_ms / 1e3) / 1e9
 
     # sanity: output sorted and values a permutation carrying their keys (outside the timed region)
-    ko64 = keys_out.to(torch.int64) & 0xFFFFFFFF
+    ko64 = order_key(torch, keys_out, args.key_type)
     ok = bool((ko64[1:] >= ko64[:-1]).all().item())
     del ko64
     if pairs:
@@ -407,12 +436,13 @@ def main():
     bin_ms = [ms for k, _, ms in recs if k == 1]
     hist_ms = [ms for k, _, ms in recs if k == 0]
     bin_avg = statistics.mean(bin_ms)
-    bytes_per_pass = n * 2 * (4 + (4 if pairs else 0))
+    bytes_per_pass = n * 2 * (kbytes + (4 if pairs else 0))
     achieved = bytes_per_pass / (bin_avg / 1e3) / 1e9
-    traffic = profiled_traffic("binning_u32_pairs" if pairs else "binning_u32_keys", n)
-    step_bytes = n * 4 + lay.num_places * bytes_per_pass
+    traffic = profiled_traffic(f"binning_{args.key_type}_{'pairs' if pairs else 'keys'}", n)
+    step_bytes = n * kbytes + lay.num_places * bytes_per_pass
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "binning_kernel<32, pairs>" if pairs else "binning_kernel<32, keys>", "peak_kind": peak_kind,
+                "traffic": traffic, "kernel": f"binning_kernel<{bits}, {'pairs' if pairs else 'keys'}>",
+                "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_per_pass, "avg_launch_ms": bin_avg}
     step_roofline = {"achieved": step_bytes / (ms_per_step / 1e3) / 1e9, "peak": peak,
                      "frac": step_bytes / (ms_per_step / 1e3) / 1e9 / peak, "algorithmic_bytes_per_step": step_bytes,
@@ -427,12 +457,12 @@ def main():
     # arrays would be served.
     e2e = None
     if args.e2e_steps > 0:
-        hk = torch.from_numpy(keys_np.view(np.int32)).pin_memory()
+        hk = torch.from_numpy(keys_np.view(kview)).pin_memory()
         hv = torch.from_numpy(vals_np.view(np.int32)).pin_memory()
         lanes = max(1, args.e2e_lanes)
         hko = [torch.empty_like(hk).pin_memory() for _ in range(lanes)]
         hvo = [torch.empty_like(hv).pin_memory() for _ in range(lanes)]
-        hws = osw.os_sort_host_workspace_bytes(kt, n, 4 if pairs else 0, 0, 32)
+        hws = osw.os_sort_host_workspace_bytes(kt, n, 4 if pairs else 0, 0, bits)
         wss = [torch.empty(hws, dtype=torch.uint8, device=dev) for _ in range(lanes)]
         streams = [torch.cuda.Stream(dev) for _ in range(lanes)]
 
@@ -441,9 +471,9 @@ def main():
             sp_b = streams[b].cuda_stream
             if pairs:
                 rc = osw.os_sort_pairs_host(kt, hk.data_ptr(), hko[b].data_ptr(), hv.data_ptr(), hvo[b].data_ptr(),
-                                            n, 0, 32, wss[b].data_ptr(), hws, sp_b)
+                                            n, 0, bits, wss[b].data_ptr(), hws, sp_b)
             else:
-                rc = osw.os_sort_keys_host(kt, hk.data_ptr(), hko[b].data_ptr(), n, 0, 32, wss[b].data_ptr(), hws,
+                rc = osw.os_sort_keys_host(kt, hk.data_ptr(), hko[b].data_ptr(), n, 0, bits, wss[b].data_ptr(), hws,
                                            sp_b)
             if rc != osw.OS_OK:
                 raise osw.OnesweepError(rc, "sort (host buffers)")
@@ -473,13 +503,12 @@ def main():
             if st != osw.OS_OK:
                 raise osw.OnesweepError(st, "device status after the end-to-end steps")
         e2e = {"value": world * n * args.e2e_steps / (float(et.item()) / 1e3) / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": hk.numel() * 4 + (hv.numel() * 4 if pairs else 0),
-               "d2h_bytes_per_step": hk.numel() * 4 + (hv.numel() * 4 if pairs else 0), "steps": args.e2e_steps,
+               "h2d_bytes_per_step": hk.numel() * kbytes + (hv.numel() * 4 if pairs else 0),
+               "d2h_bytes_per_step": hk.numel() * kbytes + (hv.numel() * 4 if pairs else 0), "steps": args.e2e_steps,
                "api": "os_sort_pairs_host" if pairs else "os_sort_keys_host",
                "pipelined": f"calls rotate over {lanes} streams with a device workspace each"}
         last = (args.e2e_steps - 1) % lanes
-        ok = np.array_equal(hko[last].numpy().view(np.uint32)[:: 1 << 16],
-                            keys_out.cpu().numpy().view(np.uint32)[:: 1 << 16])
+        ok = np.array_equal(hko[last].numpy()[:: 1 << 16], keys_out.cpu().numpy()[:: 1 << 16])
         if not ok:
             raise RuntimeError("end-to-end result differs from the device result")
 
@@ -493,20 +522,21 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = n // 2
-        times = time_oracle(sample, args.dist, seed)
+        times = time_oracle(sample, args.dist, seed, key_type=args.key_type)
         cpu = {"value": sample / times[0] / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{sample} u32 pairs (half the workload, same distribution), single-threaded C oracle, "
+               "sample": f"{sample} {args.key_type} pairs (half the workload, same distribution), single-threaded C oracle, "
                          f"{times[0]:.1f} s", "cpu": cpu_model(), "nproc": os.cpu_count()}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": workload_name(n, args.dist, args.seed, pairs), "keys_per_gpu": n,
-                       "key_type": "u32", "values": "u32 (input index)" if pairs else None, "bits": [0, 32], "places": lay.num_places,
-                       "tile_keys": lay.tile_keys, "parallelism": f"replicas x{world}",
-                       "l2": "no flush: 2 GiB of inputs per step, larger than L2"},
+            "vs_baseline": None, "dtype": args.key_type, "data": "synthetic",
+            "config": {"workload": workload_name(n, args.dist, args.seed, pairs, args.key_type), "keys_per_gpu": n,
+                       "key_type": args.key_type, "values": "u32 (input index)" if pairs else None, "bits": [0, bits],
+                       "places": lay.num_places, "tile_keys": lay.tile_keys, "parallelism": f"replicas x{world}",
+                       "l2": f"no flush: {n * (kbytes + (4 if pairs else 0)) / 2**30:.2f} GiB of inputs per step, "
+                             "larger than L2"},
             "roofline": roofline, "roofline_step": step_roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "gpu": torch.cuda.get_device_name(dev),
             "batched": batched, "serving": serving,
