@@ -99,25 +99,44 @@ __global__ void __launch_bounds__(kHistThreads, 1) histogram_kernel(HistArgs a) 
   const uint64_t tail_start = head + nvec * PER_VEC;
   const uint4* vkeys = reinterpret_cast<const uint4*>(keys + head);
 
-  const uint64_t step = (uint64_t)gridDim.x * kHistThreads * kHistVec;
-  for (uint64_t base = (uint64_t)blockIdx.x * kHistThreads * kHistVec; base < nvec; base += step) {
-    if (base + (uint64_t)kHistThreads * kHistVec <= nvec) {
-      uint4 v[kHistVec];
+  // full steps of kHistThreads * kHistVec vectors, the next step's loads in
+  // flight while this step's keys are counted; then at most one partial step
+  const uint64_t chunk = (uint64_t)kHistThreads * kHistVec;
+  const uint64_t step = (uint64_t)gridDim.x * chunk;
+  uint64_t base = (uint64_t)blockIdx.x * chunk;
+  bool have = base + chunk <= nvec;
+  uint4 v[kHistVec];
+  if (have) {
 #pragma unroll
-      for (int u = 0; u < kHistVec; ++u) v[u] = __ldcs(vkeys + base + (uint64_t)u * kHistThreads + tid);
-      K k[KPT];
+    for (int u = 0; u < kHistVec; ++u) v[u] = __ldcs(vkeys + base + (uint64_t)u * kHistThreads + tid);
+  }
+  while (have) {
+    const uint64_t next = base + step;
+    const bool more = next + chunk <= nvec;
+    uint4 w[kHistVec];
+    if (more) {
 #pragma unroll
-      for (int u = 0; u < kHistVec; ++u) unpack<KBITS>(v[u], k + u * PER_VEC);
+      for (int u = 0; u < kHistVec; ++u) w[u] = __ldcs(vkeys + next + (uint64_t)u * kHistThreads + tid);
+    }
+    K k[KPT];
 #pragma unroll
-      for (int j = 0; j < KPT; ++j) count_key(k[j]);
-    } else {
-      for (int u = 0; u < kHistVec; ++u) {
-        const uint64_t idx = base + (uint64_t)u * kHistThreads + tid;
-        if (idx < nvec) {
-          K kk[PER_VEC];
-          unpack<KBITS>(__ldcs(vkeys + idx), kk);
-          for (int j = 0; j < PER_VEC; ++j) count_key(kk[j]);
-        }
+    for (int u = 0; u < kHistVec; ++u) unpack<KBITS>(v[u], k + u * PER_VEC);
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) count_key(k[j]);
+    if (more) {
+#pragma unroll
+      for (int u = 0; u < kHistVec; ++u) v[u] = w[u];
+    }
+    base = next;
+    have = more;
+  }
+  if (base < nvec) {
+    for (int u = 0; u < kHistVec; ++u) {
+      const uint64_t idx = base + (uint64_t)u * kHistThreads + tid;
+      if (idx < nvec) {
+        K kk[PER_VEC];
+        unpack<KBITS>(__ldcs(vkeys + idx), kk);
+        for (int j = 0; j < PER_VEC; ++j) count_key(kk[j]);
       }
     }
   }
