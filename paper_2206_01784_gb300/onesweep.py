@@ -350,6 +350,59 @@ def sort_pairs(keys, values, begin_bit: int = 0, end_bit: int | None = None, key
     return keys_out, values_out
 
 
+def sort_host(keys, values=None, begin_bit: int = 0, end_bit: int | None = None, key_type=None, device=None,
+              stream=None):
+    """Stable ascending sort of keys (and uint32 values) held in host memory:
+    1-D CPU tensors (pinned ones copy asynchronously) or numpy arrays. One
+    os_sort_keys_host / os_sort_pairs_host call uploads, sorts on the GPU and
+    downloads; returns new host arrays of the same kind once the sort is done."""
+    torch = _torch()
+    is_np = not isinstance(keys, torch.Tensor)
+    k = torch.from_numpy(keys) if is_np else keys
+    if k.device.type != "cpu":
+        raise ValueError("sort_host takes host arrays; use sort_keys / sort_pairs for CUDA tensors")
+    k = k.contiguous()
+    kt = KEY_TYPES[key_type] if isinstance(key_type, str) else (
+        int(key_type) if key_type is not None else _host_key_type(k))
+    end_bit = KEY_BITS[kt] if end_bit is None else end_bit
+    n = k.numel()
+    ko = torch.empty_like(k, pin_memory=k.is_pinned())
+    v = vo = None
+    if values is not None:
+        v = (torch.from_numpy(values) if is_np else values).contiguous()
+        if v.element_size() != 4 or v.numel() != n:
+            raise ValueError("values must be 4-byte with one value per key")
+        vo = torch.empty_like(v, pin_memory=v.is_pinned())
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    nbytes = os_sort_host_workspace_bytes(kt, n, 4 if v is not None else 0, begin_bit, end_bit)
+    if nbytes == 0:
+        raise OnesweepError(OS_ERR_INVALID_ARG, "os_sort_host_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    sp = _stream_ptr(stream)
+    if v is None:
+        rc = os_sort_keys_host(kt, k.data_ptr(), ko.data_ptr(), n, begin_bit, end_bit, ws.data_ptr(), nbytes, sp)
+    else:
+        rc = os_sort_pairs_host(kt, k.data_ptr(), ko.data_ptr(), v.data_ptr(), vo.data_ptr(), n, begin_bit, end_bit,
+                                ws.data_ptr(), nbytes, sp)
+    _check(rc, "os_sort_host")
+    _check(os_workspace_status(ws.data_ptr(), sp), "device status")  # waits for the stream
+    if is_np:
+        ko = ko.numpy()
+        vo = vo.numpy() if vo is not None else None
+    return ko if v is None else (ko, vo)
+
+
+def _host_key_type(t) -> int:
+    torch = _torch()
+    by_dtype = {torch.float32: OS_KEY_F32, torch.float64: OS_KEY_F64, torch.int32: OS_KEY_I32,
+                torch.int64: OS_KEY_I64}
+    if t.dtype in by_dtype:
+        return by_dtype[t.dtype]
+    if t.element_size() in (4, 8):
+        return OS_KEY_U32 if t.element_size() == 4 else OS_KEY_U64
+    raise TypeError(f"unsupported key dtype {t.dtype}")
+
+
 def digit_histograms(keys, begin_bit: int = 0, end_bit: int | None = None, key_type=None, stream=None):
     """Digit counts and global bin offsets of every place: two int32 tensors [p, 256]."""
     torch = _torch()

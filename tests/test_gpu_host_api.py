@@ -121,3 +121,18 @@ def test_host_sort_empty_and_copy():
     keys = _keys("u32", 5000, seed=3)
     got = _run("u32", keys, workload.iota_u32(5000), 7, 7, True)
     assert np.array_equal(got[0], keys) and np.array_equal(got[1], workload.iota_u32(5000))
+
+
+@pytest.mark.parametrize("kt,pairs", [("u32", True), ("f32", False), ("u64", True), ("i32", True)])
+def test_binding_sort_host_numpy(kt, pairs):
+    # the binding's host-array helper: numpy in, numpy out, one host-buffer call
+    _dev()
+    n = 123_457
+    keys = _keys(kt, n, seed=55)
+    vals = workload.iota_u32(n) if pairs else None
+    got = osw.sort_host(keys, vals, key_type=kt)
+    exp = oracle.sort(kt, keys, vals)
+    if pairs:
+        assert np.array_equal(got[0].view(exp[0].dtype), exp[0]) and np.array_equal(got[1].view(np.uint32), exp[1])
+    else:
+        assert np.array_equal(got.view(exp.dtype), exp)
