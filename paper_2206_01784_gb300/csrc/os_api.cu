@@ -73,9 +73,7 @@ uint32_t tile_keys_for(int key_bits, bool pairs, int cfg) {
   return pairs ? binning_tile_keys64_pairs(geo) : binning_tile_keys64_keys(geo);
 }
 
-uint32_t binning_tile_keys(int key_bits, bool pairs, int bucket) {
-  return tile_keys_for(key_bits, pairs, tile_cfg(key_bits, pairs, bucket));
-}
+int binning_config(int key_bits, bool pairs, int bucket) { return tile_cfg(key_bits, pairs, bucket); }
 
 // Smallest tile over all geometries: workspaces are sized for it, so any
 // geometry fits a workspace sized once.
@@ -88,8 +86,7 @@ uint32_t min_tile_keys(int key_bits, bool pairs) {
   return t;
 }
 
-cudaError_t launch_binning(int key_bits, bool pairs, int bucket, const PassArgs& a, cudaStream_t s) {
-  const int cfg = tile_cfg(key_bits, pairs, bucket);
+cudaError_t launch_binning(int key_bits, bool pairs, int cfg, const PassArgs& a, cudaStream_t s) {
   const int flip = (a.flip_in ? 1 : 0) | (a.flip_out ? 2 : 0);
   const int seg = a.seg_offsets != nullptr;
   return kBinningLaunch[seg][key_bits == 64][pairs][flip](cfg % kGeometries, cfg / kGeometries, a, s);
@@ -177,6 +174,7 @@ struct Plan {
   int key_bits = 0;
   bool pairs = false;
   int bucket = 0;
+  int cfg = 0;               // binning variant (geometry + ranking)
   int places = 0;
   uint32_t tile = 0;
   uint32_t tiles = 0;        // tiles of a whole pass
@@ -197,7 +195,9 @@ int make_plan(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_
   plan->pairs = value_bytes == 4;
   plan->places = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
   plan->bucket = size_bucket(n);
-  plan->tile = binning_tile_keys(kb, plan->pairs, plan->bucket);
+  // the variant is read once: every launch of this sort uses the same one
+  plan->cfg = binning_config(kb, plan->pairs, plan->bucket);
+  plan->tile = tile_keys_for(kb, plan->pairs, plan->cfg);
   plan->tiles = (uint32_t)((n + plan->tile - 1) / plan->tile);
   // strips of equal length (whole tiles, at most the strip limit), so that no
   // launch is much shorter than the next one, whose status rows it clears
@@ -404,7 +404,7 @@ int run_sort(int key_type, const void* keys_in, void* keys_out, const uint32_t* 
         return OS_ERR_INVALID_ARG;
       }
       const int slot = prof_begin(1, pass, s);
-      const cudaError_t e = launch_binning(plan.key_bits, pairs, plan.bucket, a, s);
+      const cudaError_t e = launch_binning(plan.key_bits, pairs, plan.cfg, a, s);
       prof_end(slot, s);
       if (e != cudaSuccess) return OS_ERR_CUDA;
     }
@@ -429,6 +429,7 @@ struct BatchPlan {
   int key_bits = 0;
   bool pairs = false;
   int bucket = 0;
+  int cfg = 0;  // binning variant
   int places = 0;
   uint32_t tile = 0, small_max = 0;
   uint64_t max_tiles = 0, max_items = 0;
@@ -448,7 +449,8 @@ int make_batch_plan(int key_type, uint64_t n_total, int64_t num_segments, int va
   bp->pairs = value_bytes == 4;
   bp->places = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
   bp->bucket = size_bucket(S > 0 ? n_total / S : n_total);  // by the mean segment length
-  bp->tile = binning_tile_keys(kb, bp->pairs, bp->bucket);
+  bp->cfg = binning_config(kb, bp->pairs, bp->bucket);
+  bp->tile = tile_keys_for(kb, bp->pairs, bp->cfg);
   bp->small_max = batch_local_capacity(kb, bp->pairs);
   const uint32_t min_tile = min_tile_keys(kb, bp->pairs);
   bp->max_tiles = (n_total + min_tile - 1) / min_tile + S;
@@ -611,7 +613,7 @@ int run_batch(int key_type, const void* keys_in, void* keys_out, const uint32_t*
     a.skew_stride = (uint32_t)bp.places;
     a.digit_xor = pass == bp.places - 1 ? b.top_xor : 0u;
     slot = prof_begin(1, pass, s);
-    e = launch_binning(bp.key_bits, pairs, bp.bucket, a, s);
+    e = launch_binning(bp.key_bits, pairs, bp.cfg, a, s);
     prof_end(slot, s);
     if (e != cudaSuccess) return OS_ERR_CUDA;
     src_k = dst_k;

@@ -113,13 +113,16 @@ cudaError_t launch_batch_histogram(int key_bits, const BatchArgs& b, cudaStream_
 cudaError_t launch_batch_local_sort(int key_bits, bool pairs, const BatchArgs& b, cudaStream_t s);
 uint32_t batch_local_capacity(int key_bits, bool pairs);
 
-// Tile geometry of the binning kernel for a key width / payload / size bucket.
-uint32_t binning_tile_keys(int key_bits, bool pairs, int bucket);
+// Active binning variant for a key width / payload / size bucket, and the
+// tile size of a variant.
+int binning_config(int key_bits, bool pairs, int bucket);
+uint32_t tile_keys_for(int key_bits, bool pairs, int cfg);
 
 int sort_on_workspace(int key_type, const void* keys_in, void* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
                       uint64_t n, int begin_bit, int end_bit, void* ws, size_t ws_bytes, void* stream);
 
 cudaError_t launch_histogram(int key_bits, const HistArgs& a, int num_sms, cudaStream_t s);
-cudaError_t launch_binning(int key_bits, bool pairs, int bucket, const PassArgs& a, cudaStream_t s);
+// Launches variant cfg of the binning kernel (the variant a plan was made with).
+cudaError_t launch_binning(int key_bits, bool pairs, int cfg, const PassArgs& a, cudaStream_t s);
 
 }  // namespace onesweep
