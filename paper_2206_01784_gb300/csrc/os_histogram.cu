@@ -49,7 +49,12 @@ __device__ __forceinline__ void unpack<64>(const uint4& v, uint64_t* out) {
   out[1] = ((uint64_t)v.w << 32) | v.z;
 }
 
-template <int KBITS>
+// FULL: the sort covers every key bit ([0, KBITS): all places 8 bits wide,
+// digit i = byte i), so a digit is one shift and mask. FLIP: float keys (the
+// sign-flip before counting). Both are compile-time so the counting loop, the
+// kernel's whole cost (one shared-memory atomic per key and place, the issue
+// slots around it), carries no per-key branches.
+template <int KBITS, bool FULL, bool FLIP>
 __global__ void __launch_bounds__(kHistThreads, 1) histogram_kernel(HistArgs a) {
   using K = typename KeyWord<KBITS>::type;
   using L = HistLayout<KBITS>;
@@ -79,14 +84,23 @@ __global__ void __launch_bounds__(kHistThreads, 1) histogram_kernel(HistArgs a) 
   const uint32_t last_mask = (1u << (a.end_bit - (a.begin_bit + 8 * (p - 1)))) - 1u;
   // this lane's copy: counter (place, digit) at word ((place * 256 + digit) * C + copy)
   uint32_t* mine = sh + (tid & 31) % C;
+  const uint32_t top_xor = a.top_xor;
   auto count_key = [&](K k) {
-    const K o = a.flip ? flip_to_ordered(k) : k;
+    const K o = FLIP ? flip_to_ordered(k) : k;
+    if (FULL) {
 #pragma unroll
-    for (int pl = 0; pl < P; ++pl) {
-      if (pl < p) {
-        const uint32_t d =
-            digit_of(o, a.begin_bit + 8 * pl, pl == p - 1 ? last_mask : 0xFFu, pl == p - 1 ? a.top_xor : 0u);
-        atomicAdd(mine + (pl * kRadix + d) * C, 1u);
+      for (int pl = 0; pl < P; ++pl) {
+        const uint32_t d = (uint32_t)(o >> (8 * pl)) & 0xFFu;
+        atomicAdd(mine + (pl * kRadix + (pl == P - 1 ? d ^ top_xor : d)) * C, 1u);
+      }
+    } else {
+#pragma unroll
+      for (int pl = 0; pl < P; ++pl) {
+        if (pl < p) {
+          const uint32_t d =
+              digit_of(o, a.begin_bit + 8 * pl, pl == p - 1 ? last_mask : 0xFFu, pl == p - 1 ? top_xor : 0u);
+          atomicAdd(mine + (pl * kRadix + d) * C, 1u);
+        }
       }
     }
   };
@@ -179,19 +193,27 @@ __global__ void __launch_bounds__(kHistThreads, 1) histogram_kernel(HistArgs a) 
   }
 }
 
-template <int KBITS>
-cudaError_t launch_hist_t(const HistArgs& a, int grid, cudaStream_t s) {
+template <int KBITS, bool FULL, bool FLIP>
+cudaError_t launch_hist_mode(const HistArgs& a, int grid, cudaStream_t s) {
   constexpr size_t bytes = HistLayout<KBITS>::smem_bytes;
   static int configured_device = -1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (configured_device != dev) {
-    cudaError_t e = cudaFuncSetAttribute(histogram_kernel<KBITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(histogram_kernel<KBITS, FULL, FLIP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     configured_device = dev;
   }
-  histogram_kernel<KBITS><<<grid, kHistThreads, bytes, s>>>(a);
+  histogram_kernel<KBITS, FULL, FLIP><<<grid, kHistThreads, bytes, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int KBITS>
+cudaError_t launch_hist_t(const HistArgs& a, int grid, cudaStream_t s) {
+  const bool full = a.begin_bit == 0 && a.end_bit == KBITS && a.num_places == KBITS / 8;
+  if (full) return a.flip ? launch_hist_mode<KBITS, true, true>(a, grid, s) : launch_hist_mode<KBITS, true, false>(a, grid, s);
+  return a.flip ? launch_hist_mode<KBITS, false, true>(a, grid, s) : launch_hist_mode<KBITS, false, false>(a, grid, s);
 }
 
 }  // namespace
