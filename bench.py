@@ -325,12 +325,15 @@ def measure_serving(torch, dev, count: int, sweep_loads=()):
     for load in sweep_loads:
         sw = srv.run(serve.make_requests(count, seed=11, rate_per_s=load * capacity_rps), realtime=True)
         sweep.append({"load": load, "gkeys_per_s": sw["gkeys_per_s"], "p50_ms": sw["p50_ms"], "p99_ms": sw["p99_ms"],
+                      "tail_wait_ms": sw["tail_wait_ms"], "tail_service_ms": sw["tail_service_ms"],
                       "mean_batch_requests": sw["mean_batch_requests"]})
     return {"workload": f"{count} requests, Poisson arrivals at 0.7x measured capacity, sizes log-uniform 16K-64M, "
                         "u32/u64/f32 keys 60/25/15 % + u32 values, 40 GB budget, inputs copied from pinned host "
                         "memory, seed 11",
             "capacity_gkeys_per_s": cap["gkeys_per_s"], "offered_requests_per_s": 0.7 * capacity_rps,
             "gkeys_per_s": st["gkeys_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "tail_wait_ms": st["tail_wait_ms"], "tail_service_ms": st["tail_service_ms"],
+            "tail_mean_keys": st["tail_mean_keys"],
             "mean_ms": st["mean_ms"], "batches": st["batches"], "mean_batch_requests": st["mean_batch_requests"],
             "keys": st["keys"], "load_sweep": sweep}
 

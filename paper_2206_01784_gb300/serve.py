@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import bisect
 import dataclasses
+import gc
 import math
 import time
 
@@ -248,6 +249,20 @@ class Server:
     def run(self, requests: list[Request], tick_s: float = 0.0005, realtime: bool = True, order=None,
             max_batch_keys: int = 1 << 30) -> dict:
         torch = self.torch
+        # the loop is latency-bound host code: collect garbage now, not in the
+        # middle of the run (a full collection of a previous run's objects
+        # stalls every request behind it)
+        gc_was_enabled = gc.isenabled()
+        gc.collect()
+        gc.disable()
+        try:
+            return self._run(requests, tick_s, realtime, order, max_batch_keys)
+        finally:
+            if gc_was_enabled:
+                gc.enable()
+
+    def _run(self, requests, tick_s, realtime, order, max_batch_keys) -> dict:
+        torch = self.torch
         adm = Admission(self.arena, self._workspace_bytes, max_batch_keys=max_batch_keys, order=order)
         pending = sorted(requests, key=lambda r: r.arrival)
         for i, r in enumerate(pending):
@@ -314,10 +329,19 @@ class Server:
         torch.cuda.synchronize()
         lat = np.array([r.done - r.arrival for r in requests])
         span = max(r.done for r in requests) - min(r.arrival for r in requests)
+        # where the slowest 1 % spent their time: waiting for admission
+        # (memory, or the requests ahead of them) or admitted and in service
+        # (upload, queueing on a compute stream, the sort)
+        slow = np.argsort(lat)[-max(1, len(requests) // 100):]
+        wait = np.array([requests[i].admitted - requests[i].arrival for i in slow])
+        serv = np.array([requests[i].done - requests[i].admitted for i in slow])
         stats.update({
             "requests": len(requests),
             "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "tail_wait_ms": float(wait.mean() * 1e3),
+            "tail_service_ms": float(serv.mean() * 1e3),
+            "tail_mean_keys": float(np.mean([requests[i].n for i in slow])),
             "mean_ms": float(lat.mean() * 1e3),
             "span_s": float(span),
             "gkeys_per_s": stats["keys"] / span / 1e9,
