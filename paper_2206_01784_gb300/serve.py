@@ -92,11 +92,12 @@ class Arena:
 
 
 def batch_bytes(key_type: str, sizes: list[int], workspace_bytes) -> dict:
-    """Device bytes of one batch: keys and values in and out, plus workspace."""
+    """Device bytes of one batch: keys and values in and out, the segment
+    offsets, plus workspace."""
     n = sum(sizes)
     kb = KEY_BYTES[key_type]
     return {"keys_in": n * kb, "vals_in": n * 4, "keys_out": n * kb, "vals_out": n * 4,
-            "ws": workspace_bytes(key_type, n, len(sizes))}
+            "seg": 8 * (len(sizes) + 1), "ws": workspace_bytes(key_type, n, len(sizes))}
 
 
 class Admission:
@@ -196,7 +197,13 @@ class Server:
     """The GPU side: owns the arena buffer, the streams and the host data pool."""
 
     def __init__(self, budget_bytes: int, device=None, pool_words: int = 1 << 27, compute_streams: int = 2,
-                 seed: int = 11, keep_results: bool = False):
+                 seed: int = 11, keep_results: bool = False, small_batch_keys: int = 0):
+        """compute_streams: streams the batches rotate over. small_batch_keys >
+        0 gives batches of fewer keys a higher-priority stream of their own:
+        measured on the 10 000-request stream, that lowers p50 (2.8 vs 3.4 ms
+        at 0.7x load) but raises p99 (21 vs 13 ms; long sorts wait behind the
+        short ones, and at 0.9x their memory then holds up admission), so it
+        is off by default."""
         import torch
 
         self.torch = torch
@@ -208,8 +215,17 @@ class Server:
         words = workload.u32_and(pool_words, seed, 1)
         self.pool = torch.from_numpy(words.view(np.int32)).pin_memory()
         self.iota = torch.from_numpy(workload.iota_u32(1 << 26).view(np.int32)).pin_memory()
+        # page-locked staging ring for the batches' segment offsets, so the
+        # loop allocates no host or device memory per batch
+        self.seg_host = torch.empty(1 << 20, dtype=torch.int64).pin_memory()
+        self.seg_host_np = self.seg_host.numpy()
+        self.seg_pos = 0
         self.copy_stream = torch.cuda.Stream(self.device)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(compute_streams)]
+        self.small_batch_keys = small_batch_keys
+        # the short sorts' stream has the higher priority: their blocks are
+        # scheduled as soon as SMs free up, ahead of a long sort's remaining ones
+        self.small_stream = torch.cuda.Stream(self.device, priority=-1) if small_batch_keys > 0 else None
         self.keep_results = keep_results
         self.results = {}
 
@@ -221,7 +237,8 @@ class Server:
 
     def _upload(self, key_type, reqs, res):
         """Copies every request's keys and values into the batch's input
-        buffers (copy stream). Returns the device segment offsets tensor."""
+        buffers (copy stream). Returns the segment offsets (a view of the
+        batch's reservation) and the event that completes the upload."""
         torch = self.torch
         kb = KEY_BYTES[key_type]
         words_per_key = kb // 4
@@ -241,7 +258,16 @@ class Server:
                 dst_v[pos: pos + r.n].copy_(self.iota[: r.n], non_blocking=True)
                 pos += r.n
                 offs.append(pos)
-            seg = torch.tensor(offs, dtype=torch.int64).pin_memory().to(self.device, non_blocking=True)
+            m = len(offs)
+            if self.seg_pos + m > self.seg_host_np.size:
+                # wrap: the staged offsets of earlier batches must have been copied
+                self.copy_stream.synchronize()
+                self.seg_pos = 0
+            self.seg_host_np[self.seg_pos: self.seg_pos + m] = offs
+            soff = res["seg"][0]
+            seg = self.buf[soff: soff + 8 * m].view(torch.int64)
+            seg.copy_(self.seg_host[self.seg_pos: self.seg_pos + m], non_blocking=True)
+            self.seg_pos += m
         ev = torch.cuda.Event()
         ev.record(self.copy_stream)
         return seg, ev
@@ -300,10 +326,13 @@ class Server:
                 for j, r in enumerate(reqs):
                     r.batch, r.segment = batch_id, j
                 seg, up_ev = self._upload(kt, reqs, res)
-                s = self.streams[rr % len(self.streams)]
-                rr += 1
-                s.wait_event(up_ev)
                 n = sum(r.n for r in reqs)
+                if self.small_stream is not None and n < self.small_batch_keys:
+                    s = self.small_stream
+                else:
+                    s = self.streams[rr % len(self.streams)]
+                    rr += 1
+                s.wait_event(up_ev)
                 kt_id = osw.KEY_TYPES[kt]
                 ptr = lambda name: self.base + res[name][0]  # noqa: E731
                 ev_start = torch.cuda.Event(enable_timing=True)
