@@ -389,7 +389,7 @@ def main():
         else:
             rc = osw.os_sort_keys(kt, keys.data_ptr(), keys_out.data_ptr(), n, 0, bits, ws.data_ptr(), ws.numel(), sp)
         if rc != osw.OS_OK:
-            raise osw.OnesweepError(rc, "os_sort_pairs")
+            raise osw.OnesweepError(rc, "os_sort_pairs" if pairs else "os_sort_keys")
 
     warmup = max(args.warmup, 3)
     for _ in range(warmup):
@@ -399,7 +399,8 @@ def main():
     sampler = ClockSampler(gpu_smi_id(torch, local))
     sampler.start()
     time.sleep(0.3)
-    capacity = args.steps * (lay.num_places + 1) + 16
+    strips = -(-n // ((1 << 30) - 1))  # passes over 2^30 keys or more run in strips
+    capacity = args.steps * (lay.num_places * strips + 1) + 16
     osw.os_profile_start(capacity)
     barrier()
     t_start = torch.cuda.Event(enable_timing=True)
