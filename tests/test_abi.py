@@ -186,3 +186,12 @@ def test_host_api_validation_without_gpu():
     assert osw.os_sort_pairs_host(u32, hk, hko, hv, hvo, n, 0, 32, None, host_ws, 0) == osw.OS_ERR_WORKSPACE
     assert osw.os_sort_pairs_host(u32, hk, hko, hv, hvo, n, 0, 32, ws + 8, host_ws, 0) == osw.OS_ERR_INVALID_ARG
     assert osw.os_sort_keys_host(u32, None, None, 0, 0, 32, None, 0, 0) == osw.OS_OK
+
+
+def test_noalloc_scratch_covers_2_20_keys():
+    # os_sort_noalloc's fixed 16 MiB scratch holds the workspace of a 2^20-key
+    # sort of every key type, keys only or pairs (the limit its header states)
+    for name, kt in osw.KEY_TYPES.items():
+        bits = 64 if name in ("u64", "f64", "i64") else 32
+        for vb in (0, 4):
+            assert 0 < osw.os_sort_workspace_bytes(kt, 1 << 20, vb, 0, bits) <= 16 << 20, (name, vb)
