@@ -54,6 +54,8 @@ def parse_args():
     p.add_argument("--keys-only", action="store_true", help="sort keys without values")
     p.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
     p.add_argument("--serve-requests", type=int, default=10000)
+    p.add_argument("--tile-config", type=int, default=None,
+                   help="binning variant for the timed sorts (os_set_tile_config; default: the library's choice)")
     args = p.parse_args()
     if args.log2n is None:
         args.log2n = 27 if args.key_type in ("u64", "f64", "i64") else 28
@@ -365,6 +367,11 @@ def main():
 
     osw.load()
     n = 1 << args.log2n
+    if args.tile_config is not None:
+        for vb in (0, 4):
+            rc = osw.os_set_tile_config(KEY_BITS[args.key_type], vb, args.tile_config)
+            if rc != osw.OS_OK:
+                raise osw.OnesweepError(rc, "os_set_tile_config")
     seed = args.seed + 1000 * rank
     bits = KEY_BITS[args.key_type]
     kbytes = bits // 8

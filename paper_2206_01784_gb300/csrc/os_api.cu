@@ -7,6 +7,7 @@
 // workspace, zeroes its small header with one memset and enqueues the
 // launches on the caller's stream. Nothing is allocated and nothing waits on
 // the host.
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -46,11 +47,14 @@ const BinningLaunch kBinningLaunch[2][2][2][4] = {
      {OS_BINNING_ROW(64, keys, seg), OS_BINNING_ROW(64, pairs, seg)}}};
 #undef OS_BINNING_ROW
 
-// Binning kernel variants: tile geometry (3) x digit-ranking method (3);
-// variant v uses geometry v % 3 and ranking v / 3 (0: one ballot per digit
+// Binning kernel variants: tile geometry (4) x digit-ranking method (3);
+// variant v uses geometry v % 4 and ranking v / 4 (0: one ballot per digit
 // bit; 1: adaptive - ballots where the place is skewed, else the hybrid;
 // 2: hybrid - ballots and shared-memory lane masks alternating by batch).
-constexpr int kGeometries = 3;
+// Geometries 0-2 run one block per tile; geometry 3 is the persistent,
+// warp-specialised kernel (os_binning_ws.cuh), for single arrays only.
+constexpr int kGeometries = 4;
+constexpr int kPersistentGeometry = 3;
 constexpr int kTileConfigs = 3 * kGeometries;
 
 // Active variant per (key width, keys only / pairs, size bucket); set by
@@ -251,18 +255,32 @@ bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
   return x < y + bbytes && y < x + abytes;
 }
 
+}  // namespace
+
+// SM count of the current device, cached per device (one atomic word each, so
+// concurrent callers on different devices never mix their values).
 int device_sm_count() {
-  static int cached_dev = -1, cached_sms = 0;
+  constexpr int kMaxCachedDevices = 64;
+  static std::atomic<int> cache[kMaxCachedDevices];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (dev != cached_dev) {
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    cached_sms = sms;
-    cached_dev = dev;
+  if (dev >= 0 && dev < kMaxCachedDevices) {
+    const int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
   }
-  return cached_sms;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (dev >= 0 && dev < kMaxCachedDevices) cache[dev].store(sms, std::memory_order_relaxed);
+  return sms;
 }
+
+int ws_grid(uint32_t num_tiles) {
+  const int sms = device_sm_count();
+  if (sms <= 0) return 0;
+  return num_tiles < (uint32_t)sms ? (int)num_tiles : sms;
+}
+
+namespace {
 
 // Phases 1 + 2 into the workspace (header already zeroed).
 int run_histogram(const Plan& plan, int key_type, const void* keys, uint64_t n, int begin_bit, int end_bit,
@@ -450,6 +468,9 @@ int make_batch_plan(int key_type, uint64_t n_total, int64_t num_segments, int va
   bp->places = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
   bp->bucket = size_bucket(S > 0 ? n_total / S : n_total);  // by the mean segment length
   bp->cfg = binning_config(kb, bp->pairs, bp->bucket);
+  // the persistent kernel serves single arrays: a batch runs geometry 0 with
+  // the same ranking
+  if (bp->cfg % kGeometries == kPersistentGeometry) bp->cfg -= kPersistentGeometry;
   bp->tile = tile_keys_for(kb, bp->pairs, bp->cfg);
   bp->small_max = batch_local_capacity(kb, bp->pairs);
   const uint32_t min_tile = min_tile_keys(kb, bp->pairs);

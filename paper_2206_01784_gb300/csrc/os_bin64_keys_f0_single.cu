@@ -1,7 +1,7 @@
 // Instantiations of the digit-binning kernel: 64-bit keys, keys, float
 // transform mode 0 (bit 0: sign-flip on load, bit 1: undo on store),
 // one array.
-#include "os_binning.cuh"
+#include "os_binning_ws.cuh"
 
 namespace onesweep {
 

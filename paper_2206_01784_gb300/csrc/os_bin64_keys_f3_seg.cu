@@ -1,7 +1,7 @@
 // Instantiations of the digit-binning kernel: 64-bit keys, keys, float
 // transform mode 3 (bit 0: sign-flip on load, bit 1: undo on store),
 // segmented (batch) mode.
-#include "os_binning.cuh"
+#include "os_binning_ws.cuh"
 
 namespace onesweep {
 

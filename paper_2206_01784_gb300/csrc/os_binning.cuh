@@ -53,7 +53,6 @@ template <> struct TileShape<32, 2> { static constexpr int NT = 256, IPT = 16, M
 template <> struct TileShape<64, 0> { static constexpr int NT = 256, IPT = 12, MINB = 3; };
 template <> struct TileShape<64, 1> { static constexpr int NT = 256, IPT = 10, MINB = 3; };
 template <> struct TileShape<64, 2> { static constexpr int NT = 256, IPT = 8, MINB = 4; };
-constexpr int kNumGeometries = 3;
 
 // Digit-ranking variants of step 4. Two methods find the lanes sharing a
 // digit: ballots (one per digit bit, the paper's WLMS; ALU work, insensitive
@@ -126,7 +125,10 @@ struct TileCtx {
 template <bool FULL>
 __device__ __forceinline__ uint32_t wlms_rank(uint32_t* msk, uint32_t* cnt, uint32_t d, bool valid, uint32_t lane_bit,
                                               bool smask) {
-  uint32_t peers, old;
+  // the running count first: its shared-memory round trip overlaps the
+  // search for peers (the previous batch's update is already visible)
+  const uint32_t old = valid ? cnt[d] : 0u;
+  uint32_t peers;
   if (smask) {
     // every lane ORs its bit into its digit's mask word; OR commutes, so the
     // mask read back is exactly the lanes sharing the digit
@@ -137,7 +139,6 @@ __device__ __forceinline__ uint32_t wlms_rank(uint32_t* msk, uint32_t* cnt, uint
     const uint32_t valid_mask = FULL ? 0xFFFFFFFFu : __ballot_sync(0xFFFFFFFFu, valid);
     peers = digit_peers(d, valid, valid_mask);
   }
-  old = valid ? cnt[d] : 0u;
   const uint32_t below = __popc(peers & lanemask_lt());
   __syncwarp();
   if (valid && below == 0) {
@@ -502,52 +503,6 @@ __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS, CFG>::NT, BinningC
       binning_tile<KBITS, PAIRS, CFG, kRankBallot, FLIP, false>(a, smem, c);
     else
       binning_tile<KBITS, PAIRS, CFG, R0, FLIP, false>(a, smem, c);
-  }
-}
-
-template <int KBITS, bool PAIRS, int CFG, int RANK, int FLIP, bool SEG>
-cudaError_t launch_binning_one(const PassArgs& a, cudaStream_t s) {
-  using C = BinningConfig<KBITS, PAIRS, CFG>;
-  static int configured_device = -1;  // one attribute call per device switch
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (configured_device != dev) {
-    cudaError_t e = cudaFuncSetAttribute(binning_kernel<KBITS, PAIRS, CFG, RANK, FLIP, SEG>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bytes);
-    if (e != cudaSuccess) return e;
-    configured_device = dev;
-  }
-  binning_kernel<KBITS, PAIRS, CFG, RANK, FLIP, SEG><<<a.num_tiles, C::NT, C::smem_bytes, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <int KBITS, bool PAIRS, int FLIP, int RANK, bool SEG>
-cudaError_t launch_binning_flip_rank(const PassArgs& a, cudaStream_t s, int cfg) {
-  switch (cfg) {
-    case 1: return launch_binning_one<KBITS, PAIRS, 1, RANK, FLIP, SEG>(a, s);
-    case 2: return launch_binning_one<KBITS, PAIRS, 2, RANK, FLIP, SEG>(a, s);
-    default: return launch_binning_one<KBITS, PAIRS, 0, RANK, FLIP, SEG>(a, s);
-  }
-}
-
-// All tile geometries and both ranking variants for one (width, payload,
-// float transform mode, single array / segmented). The grid is a.num_tiles
-// blocks (an upper bound in segmented mode; blocks beyond the last tile exit).
-template <int KBITS, bool PAIRS, int FLIP, bool SEG>
-cudaError_t launch_binning_flip(const PassArgs& a, cudaStream_t s, int cfg, int rank) {
-  switch (rank) {
-    case kRankAdaptive: return launch_binning_flip_rank<KBITS, PAIRS, FLIP, kRankAdaptive, SEG>(a, s, cfg);
-    case kRankHybrid: return launch_binning_flip_rank<KBITS, PAIRS, FLIP, kRankHybrid, SEG>(a, s, cfg);
-    default: return launch_binning_flip_rank<KBITS, PAIRS, FLIP, kRankBallot, SEG>(a, s, cfg);
-  }
-}
-
-template <int KBITS, bool PAIRS>
-uint32_t tile_keys_t(int cfg) {
-  switch (cfg) {
-    case 1: return BinningConfig<KBITS, PAIRS, 1>::T;
-    case 2: return BinningConfig<KBITS, PAIRS, 2>::T;
-    default: return BinningConfig<KBITS, PAIRS, 0>::T;
   }
 }
 

@@ -172,8 +172,9 @@ def test_batch_cuda_graph_replay():
         assert np.array_equal(vo.cpu().numpy().view(np.uint32), ev)
 
 
-@pytest.mark.parametrize("cfg", list(range(9)))
+@pytest.mark.parametrize("cfg", list(range(12)))
 def test_batch_every_tile_config(cfg):
+    # a batch with the persistent variant selected runs geometry 0 (same ranking)
     prev = osw.os_get_tile_config(32, 4)
     try:
         assert osw.os_set_tile_config(32, 4, cfg) == osw.OS_OK

@@ -264,11 +264,14 @@ def test_lookback_wait_limit_reports_timeout():
     assert np.array_equal(to_host(out, np.uint32), oracle.sort("u32", keys))
 
 
-@pytest.mark.parametrize("cfg", list(range(9)))
+@pytest.mark.parametrize("cfg", list(range(12)))
 @pytest.mark.parametrize("kt", ["u32", "u64", "f32"])
 def test_every_tile_config(cfg, kt):
-    # every binning tile geometry gives the oracle's result (workspaces are
-    # sized for the smallest tile, so the same sizing serves all of them)
+    # every binning variant (three one-block-per-tile geometries and the
+    # persistent kernel, each with three ranking methods) gives the oracle's
+    # result (workspaces are sized for the smallest tile, so the same sizing
+    # serves all of them)
+    assert osw.os_num_tile_configs() == 12
     kb = KB[kt]
     prev = {vb: osw.os_get_tile_config(kb, vb) for vb in (0, 4)}
     try:
