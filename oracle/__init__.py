@@ -79,6 +79,14 @@ def _load(path: str | None = None):
         lib.orc_sort_passes.argtypes = [i32, vp, vp, u64, i32, i32, i32, i32, vp, vp]
         lib.orc_sort_segments.restype = i32
         lib.orc_sort_segments.argtypes = [i32, vp, vp, vp, i64, i32, i32, i32, vp, vp]
+        lib.orc_histograms_ex.restype = None
+        lib.orc_histograms_ex.argtypes = [i32, vp, u64, i32, i32, i32, i32, vp]
+        lib.orc_bin_offsets_ex.restype = None
+        lib.orc_bin_offsets_ex.argtypes = [i32, vp, u64, i32, i32, i32, i32, vp]
+        lib.orc_sort_ex.restype = i32
+        lib.orc_sort_ex.argtypes = [i32, vp, vp, u64, i32, i32, i32, i32, vp, vp]
+        lib.orc_sort_segments_ex.restype = i32
+        lib.orc_sort_segments_ex.argtypes = [i32, vp, vp, vp, i64, i32, i32, i32, i32, vp, vp]
         lib.orc_tile_digit_counts.restype = i32
         lib.orc_tile_digit_counts.argtypes = [i32, vp, u64, i32, i32, u64, vp]
         _lib = lib
@@ -125,32 +133,37 @@ def exclusive_sum(counts) -> np.ndarray:
 
 
 def histograms(key_type: str, keys, begin_bit: int = 0, end_bit: int | None = None,
-               radix_bits: int = RADIX_BITS) -> np.ndarray:
-    """[p, 2^radix_bits] digit counts of every place (uint64)."""
+               radix_bits: int = RADIX_BITS, descending: bool = False) -> np.ndarray:
+    """[p, 2^radix_bits] digit counts of every place (uint64); for a descending
+    sort, of the complemented digits the passes bin by."""
     end_bit = key_bits(key_type) if end_bit is None else end_bit
     k = _keys(key_type, keys)
     p = num_places(begin_bit, end_bit, radix_bits)
     out = np.zeros((max(p, 1), 1 << radix_bits), np.uint64)
-    _load().orc_histograms(_kt(key_type), _ptr(k), k.size, begin_bit, end_bit, radix_bits, _ptr(out))
+    _load().orc_histograms_ex(_kt(key_type), _ptr(k), k.size, begin_bit, end_bit, radix_bits, int(descending),
+                              _ptr(out))
     return out[:p]
 
 
 def bin_offsets(key_type: str, keys, begin_bit: int = 0, end_bit: int | None = None,
-                radix_bits: int = RADIX_BITS) -> np.ndarray:
+                radix_bits: int = RADIX_BITS, descending: bool = False) -> np.ndarray:
     """[p, 2^radix_bits] global bin offsets (exclusive sums of the histograms)."""
     end_bit = key_bits(key_type) if end_bit is None else end_bit
     k = _keys(key_type, keys)
     p = num_places(begin_bit, end_bit, radix_bits)
     out = np.zeros((max(p, 1), 1 << radix_bits), np.uint64)
-    _load().orc_bin_offsets(_kt(key_type), _ptr(k), k.size, begin_bit, end_bit, radix_bits, _ptr(out))
+    _load().orc_bin_offsets_ex(_kt(key_type), _ptr(k), k.size, begin_bit, end_bit, radix_bits, int(descending),
+                               _ptr(out))
     return out[:p]
 
 
 def sort(key_type: str, keys, vals=None, begin_bit: int = 0, end_bit: int | None = None,
-         radix_bits: int = RADIX_BITS, passes: int | None = None):
-    """Stable ascending LSD sort. Returns keys, or (keys, vals) when vals is given.
+         radix_bits: int = RADIX_BITS, passes: int | None = None, descending: bool = False):
+    """Stable ascending (or stable descending) LSD sort. Returns keys, or
+    (keys, vals) when vals is given.
 
-    ``passes`` stops after that many binning passes (default: all p)."""
+    ``passes`` stops after that many binning passes (default: all p; an
+    ascending sort only)."""
     end_bit = key_bits(key_type) if end_bit is None else end_bit
     k = _keys(key_type, keys)
     ko = np.empty_like(k)
@@ -158,8 +171,10 @@ def sort(key_type: str, keys, vals=None, begin_bit: int = 0, end_bit: int | None
     vo = None if v is None else np.empty_like(v)
     lib = _load()
     if passes is None:
-        rc = lib.orc_sort(_kt(key_type), _ptr(k), _ptr(v), k.size, begin_bit, end_bit, radix_bits,
-                          _ptr(ko), _ptr(vo))
+        rc = lib.orc_sort_ex(_kt(key_type), _ptr(k), _ptr(v), k.size, begin_bit, end_bit, radix_bits,
+                             int(descending), _ptr(ko), _ptr(vo))
+    elif descending:
+        raise ValueError("passes applies to ascending sorts")
     else:
         rc = lib.orc_sort_passes(_kt(key_type), _ptr(k), _ptr(v), k.size, begin_bit, end_bit, radix_bits,
                                  passes, _ptr(ko), _ptr(vo))
@@ -169,7 +184,7 @@ def sort(key_type: str, keys, vals=None, begin_bit: int = 0, end_bit: int | None
 
 
 def sort_segments(key_type: str, keys, offsets, vals=None, begin_bit: int = 0, end_bit: int | None = None,
-                  radix_bits: int = RADIX_BITS):
+                  radix_bits: int = RADIX_BITS, descending: bool = False):
     """Each segment [offsets[s], offsets[s+1]) sorted on its own."""
     end_bit = key_bits(key_type) if end_bit is None else end_bit
     k = _keys(key_type, keys)
@@ -177,8 +192,8 @@ def sort_segments(key_type: str, keys, offsets, vals=None, begin_bit: int = 0, e
     ko = np.empty_like(k)
     v = None if vals is None else np.ascontiguousarray(vals, dtype=np.uint32)
     vo = None if v is None else np.empty_like(v)
-    rc = _load().orc_sort_segments(_kt(key_type), _ptr(k), _ptr(v), _ptr(off), off.size - 1, begin_bit,
-                                   end_bit, radix_bits, _ptr(ko), _ptr(vo))
+    rc = _load().orc_sort_segments_ex(_kt(key_type), _ptr(k), _ptr(v), _ptr(off), off.size - 1, begin_bit,
+                                      end_bit, radix_bits, int(descending), _ptr(ko), _ptr(vo))
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
     return ko if v is None else (ko, vo)

@@ -38,7 +38,11 @@
  *  - a bit range [begin_bit, end_bit): places start at begin_bit and go
  *    upward; when (end_bit - begin_bit) is not a multiple of d the last (most
  *    significant) place is narrower;
- *  - equal keys keep their input order.
+ *  - equal keys keep their input order;
+ *  - descending order (the paper sorts ascending only, Section 4): equal
+ *    keys still keep their input order, and every place bins by the
+ *    complement of its digit within the place (largest digit first), which is
+ *    the ascending sort of the complemented field.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -110,6 +114,13 @@ static uint64_t digit_of(uint64_t u, int shift, int width) {
     return (u >> shift) & mask;
 }
 
+/* The digit a pass bins by: the digit itself, or for a descending sort its
+   complement within the place (2^width - 1 - digit). */
+static uint64_t sort_digit(uint64_t u, int shift, int width, int descending) {
+    uint64_t d = digit_of(u, shift, width);
+    return descending ? ((1ULL << width) - 1ULL) - d : d;
+}
+
 static uint64_t load_key(int key_type, const void *keys, uint64_t i) {
     if (orc_key_bits(key_type) == 64) return ((const uint64_t *)keys)[i];
     return ((const uint32_t *)keys)[i];
@@ -140,8 +151,8 @@ void orc_exclusive_sum(const uint64_t *in, int64_t count, uint64_t *out) {
  * phase 1, "Histograms of global digit counts"; Figure 5).
  * hist is [p][2^radix_bits], row `place` counts the digits of that place.
  */
-void orc_histograms(int key_type, const void *keys, uint64_t n, int begin_bit, int end_bit,
-                    int radix_bits, uint64_t *hist) {
+void orc_histograms_ex(int key_type, const void *keys, uint64_t n, int begin_bit, int end_bit,
+                       int radix_bits, int descending, uint64_t *hist) {
     int p = orc_num_places(begin_bit, end_bit, radix_bits);
     uint64_t r = 1ULL << radix_bits;
     memset(hist, 0, sizeof(uint64_t) * (size_t)(p * r));
@@ -150,23 +161,33 @@ void orc_histograms(int key_type, const void *keys, uint64_t n, int begin_bit, i
         for (int place = 0; place < p; ++place) {
             int shift, width;
             place_bits(begin_bit, end_bit, radix_bits, place, &shift, &width);
-            hist[place * r + digit_of(u, shift, width)] += 1;
+            hist[place * r + sort_digit(u, shift, width, descending)] += 1;
         }
     }
+}
+
+void orc_histograms(int key_type, const void *keys, uint64_t n, int begin_bit, int end_bit,
+                    int radix_bits, uint64_t *hist) {
+    orc_histograms_ex(key_type, keys, n, begin_bit, end_bit, radix_bits, 0, hist);
 }
 
 /*
  * Global bin offsets of every place: the exclusive prefix sum of each place's
  * histogram (Section 3, phase 2, "Prefix sums of global digit counts").
  */
-void orc_bin_offsets(int key_type, const void *keys, uint64_t n, int begin_bit, int end_bit,
-                     int radix_bits, uint64_t *offsets) {
+void orc_bin_offsets_ex(int key_type, const void *keys, uint64_t n, int begin_bit, int end_bit,
+                        int radix_bits, int descending, uint64_t *offsets) {
     int p = orc_num_places(begin_bit, end_bit, radix_bits);
     uint64_t r = 1ULL << radix_bits;
     uint64_t *hist = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(p * r + 1));
-    orc_histograms(key_type, keys, n, begin_bit, end_bit, radix_bits, hist);
+    orc_histograms_ex(key_type, keys, n, begin_bit, end_bit, radix_bits, descending, hist);
     for (int place = 0; place < p; ++place) orc_exclusive_sum(hist + place * r, (int64_t)r, offsets + place * r);
     free(hist);
+}
+
+void orc_bin_offsets(int key_type, const void *keys, uint64_t n, int begin_bit, int end_bit,
+                     int radix_bits, uint64_t *offsets) {
+    orc_bin_offsets_ex(key_type, keys, n, begin_bit, end_bit, radix_bits, 0, offsets);
 }
 
 /*
@@ -177,14 +198,14 @@ void orc_bin_offsets(int key_type, const void *keys, uint64_t n, int begin_bit, 
  * computes exactly that; values follow their keys.
  */
 static void binning_pass(const uint64_t *in, const uint32_t *vin, uint64_t n, int shift, int width,
-                         uint64_t *out, uint32_t *vout) {
+                         int descending, uint64_t *out, uint32_t *vout) {
     uint64_t r = 1ULL << width;
     uint64_t *count = (uint64_t *)calloc((size_t)r, sizeof(uint64_t));
     uint64_t *cursor = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)r);
-    for (uint64_t i = 0; i < n; ++i) count[digit_of(in[i], shift, width)] += 1;
+    for (uint64_t i = 0; i < n; ++i) count[sort_digit(in[i], shift, width, descending)] += 1;
     orc_exclusive_sum(count, (int64_t)r, cursor);
     for (uint64_t i = 0; i < n; ++i) {
-        uint64_t d = digit_of(in[i], shift, width);
+        uint64_t d = sort_digit(in[i], shift, width, descending);
         uint64_t dst = cursor[d]++;
         out[dst] = in[i];
         if (vin) vout[dst] = vin[i];
@@ -196,11 +217,12 @@ static void binning_pass(const uint64_t *in, const uint32_t *vin, uint64_t n, in
 /*
  * LSD radix sort (Section 1; Section 3 phase 3): p binning passes, least
  * significant place first. vals_in / vals_out may be NULL (keys only).
- * keys_out receives the input key bits in stable ascending order of the
- * ordered field bits [begin_bit, end_bit). Returns 0, or -1 on bad arguments.
+ * keys_out receives the input key bits in stable ascending (descending != 0:
+ * stable descending) order of the ordered field bits [begin_bit, end_bit).
+ * Returns 0, or -1 on bad arguments.
  */
-int orc_sort(int key_type, const void *keys_in, const uint32_t *vals_in, uint64_t n, int begin_bit,
-             int end_bit, int radix_bits, void *keys_out, uint32_t *vals_out) {
+int orc_sort_ex(int key_type, const void *keys_in, const uint32_t *vals_in, uint64_t n, int begin_bit,
+                int end_bit, int radix_bits, int descending, void *keys_out, uint32_t *vals_out) {
     int kbits = orc_key_bits(key_type);
     if (begin_bit < 0 || end_bit > kbits || begin_bit > end_bit || radix_bits < 1 || radix_bits > 16) return -1;
     if ((vals_in == NULL) != (vals_out == NULL)) return -1;
@@ -217,7 +239,7 @@ int orc_sort(int key_type, const void *keys_in, const uint32_t *vals_in, uint64_
     for (int place = 0; place < p; ++place) {
         int shift, width;
         place_bits(begin_bit, end_bit, radix_bits, place, &shift, &width);
-        binning_pass(a, va, n, shift, width, b, vb);
+        binning_pass(a, va, n, shift, width, descending, b, vb);
         uint64_t *t = a; a = b; b = t;
         uint32_t *tv = va; va = vb; vb = tv;
     }
@@ -225,6 +247,11 @@ int orc_sort(int key_type, const void *keys_in, const uint32_t *vals_in, uint64_
     if (vals_out) memcpy(vals_out, va, sizeof(uint32_t) * (size_t)n);
     free(a); free(b); free(va); free(vb);
     return 0;
+}
+
+int orc_sort(int key_type, const void *keys_in, const uint32_t *vals_in, uint64_t n, int begin_bit,
+             int end_bit, int radix_bits, void *keys_out, uint32_t *vals_out) {
+    return orc_sort_ex(key_type, keys_in, vals_in, n, begin_bit, end_bit, radix_bits, 0, keys_out, vals_out);
 }
 
 /*
@@ -242,19 +269,26 @@ int orc_sort_passes(int key_type, const void *keys_in, const uint32_t *vals_in, 
 }
 
 /* Segmented form: each segment [offsets[s], offsets[s+1]) sorted on its own. */
-int orc_sort_segments(int key_type, const void *keys_in, const uint32_t *vals_in, const uint64_t *offsets,
-                      int64_t num_segments, int begin_bit, int end_bit, int radix_bits, void *keys_out,
-                      uint32_t *vals_out) {
+int orc_sort_segments_ex(int key_type, const void *keys_in, const uint32_t *vals_in, const uint64_t *offsets,
+                         int64_t num_segments, int begin_bit, int end_bit, int radix_bits, int descending,
+                         void *keys_out, uint32_t *vals_out) {
     size_t kb = (size_t)orc_key_bits(key_type) / 8;
     for (int64_t s = 0; s < num_segments; ++s) {
         uint64_t lo = offsets[s], hi = offsets[s + 1];
         if (hi < lo) return -1;
-        int rc = orc_sort(key_type, (const char *)keys_in + lo * kb, vals_in ? vals_in + lo : NULL, hi - lo,
-                          begin_bit, end_bit, radix_bits, (char *)keys_out + lo * kb,
-                          vals_out ? vals_out + lo : NULL);
+        int rc = orc_sort_ex(key_type, (const char *)keys_in + lo * kb, vals_in ? vals_in + lo : NULL, hi - lo,
+                             begin_bit, end_bit, radix_bits, descending, (char *)keys_out + lo * kb,
+                             vals_out ? vals_out + lo : NULL);
         if (rc) return rc;
     }
     return 0;
+}
+
+int orc_sort_segments(int key_type, const void *keys_in, const uint32_t *vals_in, const uint64_t *offsets,
+                      int64_t num_segments, int begin_bit, int end_bit, int radix_bits, void *keys_out,
+                      uint32_t *vals_out) {
+    return orc_sort_segments_ex(key_type, keys_in, vals_in, offsets, num_segments, begin_bit, end_bit, radix_bits,
+                                0, keys_out, vals_out);
 }
 
 /*

@@ -107,8 +107,52 @@ def pin_signed():
     return bool(np.array_equal(vo, perm.astype(np.uint32)) and np.array_equal(ko, bits[perm]))
 
 
+def pin_descending_bruteforce():
+    # every array of length <= 4 over 3-bit keys (digit widths 1-3), and
+    # seeded length-9 arrays: the stable descending order of Python's sorted
+    # (reverse=True keeps equal keys in input order)
+    import itertools
+    rng = np.random.default_rng(5)
+    cases = [np.array(c, np.uint32) for n in range(1, 5) for c in itertools.product(range(8), repeat=n)]
+    cases += [rng.integers(0, 8, 9).astype(np.uint32) for _ in range(200)]
+    for keys in cases:
+        for d in (1, 2, 3):
+            _, vo = oracle.sort("u32", keys, np.arange(keys.size, dtype=np.uint32), 0, 3, d, descending=True)
+            exp = sorted(range(keys.size), key=lambda i: int(keys[i]), reverse=True)
+            if vo.tolist() != exp:
+                return False
+    return True
+
+
+def pin_descending_numpy():
+    ok = True
+    for kt, begin, end in (("u32", 0, 32), ("u32", 3, 29), ("u64", 0, 64), ("u64", 5, 50)):
+        keys = workload.keys(kt, "and3", 5000, seed=6)
+        ko, vo = oracle.sort(kt, keys, workload.iota_u32(keys.size), begin, end, descending=True)
+        f = _field(keys, begin, end)
+        perm = np.argsort(f.max() - f, kind="stable")  # descending field, ties in input order
+        ok &= np.array_equal(vo, perm.astype(np.uint32)) and np.array_equal(ko, keys[perm])
+        h = oracle.histograms(kt, keys, begin, end, descending=True)
+        for place in range(h.shape[0]):
+            s = begin + 8 * place
+            w = min(s + 8, end) - s
+            d = ((1 << w) - 1) - _field(keys, s, s + w).astype(np.int64)
+            ok &= np.array_equal(h[place], np.bincount(d, minlength=256))
+    # float keys: IEEE descending, +0.0 before -0.0, ties in input order
+    bits = workload.keys("f32", "normal", 5000, seed=9)
+    ko, vo = oracle.sort("f32", bits, workload.iota_u32(bits.size), descending=True)
+    x = bits.view(np.float32)
+    r = np.lexsort((np.arange(x.size), np.where(np.signbit(x), 1, 0), -x))
+    ok &= np.array_equal(vo, r.astype(np.uint32))
+    # signed keys
+    bits = workload.keys("i64", "uniform", 3000, seed=2)
+    _, vo = oracle.sort("i64", bits, workload.iota_u32(bits.size), descending=True)
+    ok &= np.array_equal(vo, np.argsort(-bits.view(np.int64).astype(object), kind="stable").astype(np.uint32))
+    return bool(ok)
+
+
 PINS = [pin_signed, pin_exclusive_sum, pin_flag_scan, pin_sort_numpy, pin_float, pin_histograms, pin_float_np,
-        pin_tile_counts]
+        pin_tile_counts, pin_descending_bruteforce, pin_descending_numpy]
 
 
 def failing(lib_path=None):
