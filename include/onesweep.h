@@ -37,7 +37,7 @@
  *  - n must be below 2^32 (output positions are 32-bit); larger n returns
  *    OS_ERR_TOO_LARGE. The chained scan keeps 30-bit counts, so passes over
  *    2^30 keys or more run strip by strip (Section 3, "Handling very large
- *    problems"; see os_debug_set_strip_keys).
+ *    problems"; onesweep_debug.h can shorten strips for tests).
  *  - Inputs are never modified. Input, output and workspace ranges must not
  *    overlap (OS_ERR_INVALID_ARG). Key pointers must be aligned to the key
  *    width and value pointers to 4 bytes.
@@ -191,6 +191,17 @@ OS_API int os_workspace_status(const void *ws, void *stream);
 OS_API const char *os_status_string(int status);
 
 /*
+ * What this library was built for (not part of the method). os_build_info()
+ * returns a static string naming the virtual architectures its device code
+ * was compiled for ("cuda_arch_list=1030" for sm_103a); it needs no GPU.
+ * os_binary_version() asks the driver for the architecture of the device code
+ * it loaded on the current device (cudaFuncAttributes::binaryVersion, 103 for
+ * sm_103a), or returns a negative CUDA error code.
+ */
+OS_API const char *os_build_info(void);
+OS_API int os_binary_version(void);
+
+/*
  * os_sort_noalloc - the same sort as os_sort_keys / os_sort_pairs for callers
  * that cannot allocate device memory. The paper has no counterpart; this is a
  * convenience of this library.
@@ -210,9 +221,11 @@ OS_API const char *os_status_string(int status);
  * 16 MiB returns OS_ERR_SCRATCH_LIMIT and does nothing. Up to 2^20 keys always
  * fit, for every key type, with or without values.
  *
- * Arguments as os_sort_pairs; vals_in and vals_out both NULL sorts keys only.
- * The sort runs on the current device and `stream` must belong to it. The
- * first call on a device looks up that device's copy of the scratch array
+ * Arguments as os_sort_pairs; vals_in and vals_out both NULL sorts keys only
+ * (exactly one of them NULL is OS_ERR_INVALID_ARG). The sort runs on the
+ * current device and `stream` must belong to it. The first call on a device -
+ * and the first after that device's context was recreated, e.g. by
+ * cudaDeviceReset - looks up the device's copy of the scratch array
  * (cudaGetSymbolAddress), so make that first call before any stream capture
  * begins. All calls share the one array per device and each call leaves its
  * contents behind (the sort re-initialises what it needs): calls that may
@@ -254,35 +267,14 @@ OS_API int os_set_tile_config_bucket(int key_bits, int value_bytes, int bucket, 
 OS_API int os_get_tile_config_bucket(int key_bits, int value_bytes, int bucket);
 
 /*
- * Fault injection for tests of the look-back wait limit (not part of the
- * method). With tile >= 0, every later binning pass skips all status-counter
- * publishes of that tile, so the tiles after it wait until `spin_limit`
- * polls have gone by, record OS_ERR_TIMEOUT and finish with invalid output.
- * tile = -1 switches injection off; spin_limit = 0 restores the default
- * limit. Process-wide setting, applied at launch time.
- */
-OS_API void os_debug_set_lookback_fault(int64_t tile, uint32_t spin_limit);
-
-/*
- * Strip length of single-array sorts (Section 3, "Handling very large
- * problems"): a pass over more keys than one strip runs as one binning launch
- * per strip, each strip a chain of its own, the next strip's bins starting
- * where the previous strip's ended. Strips are at most 2^30 - 1 keys (every
- * look-back count stays below the 30-bit limit) and of equal length in whole
- * tiles; this sets that maximum, so tests can run the multi-strip path on
- * small inputs. `keys` is clamped to [2^16, 2^30 - 1]; 0 restores the
- * default. Returns the value set. Process-wide, applied when a sort is planned; a workspace sized
- * for n fits any strip length.
- */
-OS_API uint64_t os_debug_set_strip_keys(uint64_t keys);
-
-/*
  * Launch timing for benchmarks (not part of the method). os_profile_start
  * makes every later kernel launch of the library record a CUDA event pair on
  * its own stream, for up to `capacity` launches. os_profile_stop waits for
  * those events, writes up to `max` records to `out` (host array), stores how
  * many launches were recorded in *count, releases the events and switches
- * recording off. Process-wide, not thread-safe. Both return an os_status.
+ * recording off. Process-wide (the recording table is guarded by a lock, but
+ * the timings mean something only for launches from one thread). Both return
+ * an os_status.
  */
 typedef struct {
     int kernel;   /* 0 = histogram (phases 1-2), 1 = digit binning (phase 3),
@@ -293,6 +285,33 @@ typedef struct {
 
 OS_API int os_profile_start(int capacity);
 OS_API int os_profile_stop(os_launch_time *out, int max, int *count);
+
+/*
+ * Per-call options (not part of the method): the same sorts as os_sort_keys,
+ * os_sort_pairs and os_sort_batch with the binning variant chosen by the
+ * caller rather than read from the process-wide table above, so that
+ * concurrent callers (several host threads, several streams) can each use
+ * their own. opt == NULL or opt->tile_config == -1 means the process-wide
+ * choice for the sort's size bucket; any other value must be below
+ * os_num_tile_configs() (else OS_ERR_INVALID_ARG). Results are identical for
+ * every variant. `reserved` must be 0. The library holds no other per-call
+ * state: calls on different streams with different workspaces may run
+ * concurrently from any number of host threads.
+ */
+typedef struct {
+    int tile_config;
+    uint32_t reserved;
+} os_sort_options;
+
+OS_API int os_sort_keys_ex(int key_type, const void *keys_in, void *keys_out, uint64_t n, int begin_bit,
+                           int end_bit, void *ws, size_t ws_bytes, void *stream, const os_sort_options *opt);
+OS_API int os_sort_pairs_ex(int key_type, const void *keys_in, void *keys_out, const uint32_t *vals_in,
+                            uint32_t *vals_out, uint64_t n, int begin_bit, int end_bit, void *ws, size_t ws_bytes,
+                            void *stream, const os_sort_options *opt);
+OS_API int os_sort_batch_ex(int key_type, const void *keys_in, void *keys_out, const uint32_t *vals_in,
+                            uint32_t *vals_out, const uint64_t *seg_offsets, int num_segments, uint64_t n_total,
+                            int begin_bit, int end_bit, void *ws, size_t ws_bytes, void *stream,
+                            const os_sort_options *opt);
 
 #ifdef __cplusplus
 }

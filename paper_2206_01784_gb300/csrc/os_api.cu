@@ -11,8 +11,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/onesweep.h"
+#include "../../include/onesweep_debug.h"
 #include "os_common.cuh"
 #include "os_internal.h"
 
@@ -58,7 +60,9 @@ constexpr int kPersistentGeometry = 3;
 constexpr int kTileConfigs = 3 * kGeometries;
 
 // Active variant per (key width, keys only / pairs, size bucket); set by
-// os_set_tile_config / os_set_tile_config_bucket (the autotuner's hooks).
+// os_set_tile_config / os_set_tile_config_bucket (the autotuner's hooks) and
+// read once per sort when it is planned, with atomic loads and stores (a
+// sort may also name its variant itself: os_sort_*_ex).
 // Default: geometry 0 with adaptive ranking (the fastest measured on GB300 at
 // 2^28 keys across the key distributions).
 constexpr int kDefaultTileConfig = kGeometries + 0;
@@ -69,7 +73,12 @@ int g_tile_cfg[2][2][kSizeBuckets] = {{OS_FOUR_DEFAULTS, OS_FOUR_DEFAULTS}, {OS_
 
 int size_bucket(uint64_t n) { return n < (1u << 16) ? 0 : n < (1u << 20) ? 1 : n < (1u << 24) ? 2 : 3; }
 
-int& tile_cfg(int key_bits, bool pairs, int bucket) { return g_tile_cfg[key_bits == 64][pairs][bucket]; }
+int get_tile_cfg(int key_bits, bool pairs, int bucket) {
+  return __atomic_load_n(&g_tile_cfg[key_bits == 64][pairs][bucket], __ATOMIC_RELAXED);
+}
+void set_tile_cfg(int key_bits, bool pairs, int bucket, int cfg) {
+  __atomic_store_n(&g_tile_cfg[key_bits == 64][pairs][bucket], cfg, __ATOMIC_RELAXED);
+}
 
 uint32_t tile_keys_for(int key_bits, bool pairs, int cfg) {
   const int geo = cfg % kGeometries;
@@ -77,7 +86,7 @@ uint32_t tile_keys_for(int key_bits, bool pairs, int cfg) {
   return pairs ? binning_tile_keys64_pairs(geo) : binning_tile_keys64_keys(geo);
 }
 
-int binning_config(int key_bits, bool pairs, int bucket) { return tile_cfg(key_bits, pairs, bucket); }
+int binning_config(int key_bits, bool pairs, int bucket) { return get_tile_cfg(key_bits, pairs, bucket); }
 
 // Smallest tile over all geometries: workspaces are sized for it, so any
 // geometry fits a workspace sized once.
@@ -105,7 +114,7 @@ namespace {
 constexpr uint64_t kMaxKeys = 1ull << 32;
 constexpr uint64_t kStripKeys = (1ull << 30) - 1;  // every count of a strip fits 30 bits
 constexpr uint64_t kMinStripKeys = 1ull << 16;
-uint64_t g_strip_keys = kStripKeys;  // shorter strips: os_debug_set_strip_keys
+std::atomic<uint64_t> g_strip_keys{kStripKeys};  // shorter strips: os_debug_set_strip_keys
 constexpr size_t kAlign = 256;
 constexpr uint32_t kDefaultSpinLimit = 1u << 22;
 
@@ -117,14 +126,18 @@ constexpr size_t kDoneWord = 1;
 constexpr size_t kTileCounterWord = 16;
 constexpr size_t kSkewWord = 32;  // 8 skewed-place flags of a single sort
 
-int64_t g_fault_tile = -1;
-uint32_t g_spin_limit = kDefaultSpinLimit;
+// Test hooks (onesweep_debug.h), read once per sort when it is planned.
+std::atomic<int64_t> g_fault_tile{-1};
+std::atomic<uint32_t> g_spin_limit{kDefaultSpinLimit};
 
-// Launch timing (os_profile_start / os_profile_stop).
+// Launch timing (os_profile_start / os_profile_stop): a table guarded by a
+// lock; g_prof_on lets sorts skip the lock while timing is off.
 struct ProfiledLaunch {
   cudaEvent_t start, stop;
   int kernel, pass;
 };
+std::mutex g_prof_mutex;
+std::atomic<bool> g_prof_on{false};
 ProfiledLaunch* g_prof = nullptr;
 int g_prof_capacity = 0;
 int g_prof_used = 0;
@@ -132,6 +145,8 @@ int g_prof_seen = 0;
 
 // Records the start event of a launch if profiling is on; returns its slot.
 int prof_begin(int kernel, int pass, cudaStream_t s) {
+  if (!g_prof_on.load(std::memory_order_acquire)) return -1;
+  std::lock_guard<std::mutex> lock(g_prof_mutex);
   if (!g_prof) return -1;
   ++g_prof_seen;
   if (g_prof_used >= g_prof_capacity) return -1;
@@ -143,7 +158,9 @@ int prof_begin(int kernel, int pass, cudaStream_t s) {
 }
 
 void prof_end(int slot, cudaStream_t s) {
-  if (slot >= 0) cudaEventRecord(g_prof[slot].stop, s);
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lock(g_prof_mutex);
+  if (g_prof && slot < g_prof_capacity) cudaEventRecord(g_prof[slot].stop, s);
 }
 
 size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -180,6 +197,8 @@ struct Plan {
   int bucket = 0;
   int cfg = 0;               // binning variant (geometry + ranking)
   int places = 0;
+  int64_t fault_tile = -1;   // test hooks, read once
+  uint32_t spin_limit = 0;
   uint32_t tile = 0;
   uint32_t tiles = 0;        // tiles of a whole pass
   uint64_t strip = 0;        // keys per strip (a multiple of the tile)
@@ -189,7 +208,9 @@ struct Plan {
   os_workspace_layout layout{};
 };
 
-int make_plan(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_bit, Plan* plan) {
+// cfg_override: the caller's binning variant, or -1 for the process-wide one.
+int make_plan(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_bit, Plan* plan,
+              int cfg_override = -1) {
   const int kb = key_bits_of(key_type);
   if (kb == 0) return OS_ERR_INVALID_ARG;
   if (value_bytes != 0 && value_bytes != 4) return OS_ERR_INVALID_ARG;
@@ -200,12 +221,15 @@ int make_plan(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_
   plan->places = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
   plan->bucket = size_bucket(n);
   // the variant is read once: every launch of this sort uses the same one
-  plan->cfg = binning_config(kb, plan->pairs, plan->bucket);
+  if (cfg_override >= kTileConfigs) return OS_ERR_INVALID_ARG;
+  plan->cfg = cfg_override >= 0 ? cfg_override : binning_config(kb, plan->pairs, plan->bucket);
+  plan->fault_tile = g_fault_tile.load(std::memory_order_relaxed);
+  plan->spin_limit = g_spin_limit.load(std::memory_order_relaxed);
   plan->tile = tile_keys_for(kb, plan->pairs, plan->cfg);
   plan->tiles = (uint32_t)((n + plan->tile - 1) / plan->tile);
   // strips of equal length (whole tiles, at most the strip limit), so that no
   // launch is much shorter than the next one, whose status rows it clears
-  const uint64_t max_strip = g_strip_keys / plan->tile * plan->tile;
+  const uint64_t max_strip = g_strip_keys.load(std::memory_order_relaxed) / plan->tile * plan->tile;
   const uint64_t want = n == 0 ? 1u : (n + max_strip - 1) / max_strip;
   uint64_t strip = (n + want - 1) / want;
   strip = (strip + plan->tile - 1) / plan->tile * plan->tile;
@@ -310,11 +334,11 @@ int run_histogram(const Plan& plan, int key_type, const void* keys, uint64_t n, 
 }
 
 int run_sort(int key_type, const void* keys_in, void* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
-             uint64_t n, int begin_bit, int end_bit, void* ws, size_t ws_bytes, void* stream) {
+             uint64_t n, int begin_bit, int end_bit, void* ws, size_t ws_bytes, void* stream, int cfg_override = -1) {
   const bool pairs = vals_in != nullptr || vals_out != nullptr;
   if (pairs && (vals_in == nullptr || vals_out == nullptr)) return OS_ERR_INVALID_ARG;
   Plan plan;
-  int rc = make_plan(key_type, n, pairs ? 4 : 0, begin_bit, end_bit, &plan);
+  int rc = make_plan(key_type, n, pairs ? 4 : 0, begin_bit, end_bit, &plan, cfg_override);
   if (rc != OS_OK) return rc;
   if (n == 0) return OS_OK;
   const size_t kbytes = (size_t)n * (plan.key_bits / 8);
@@ -413,8 +437,8 @@ int run_sort(int key_type, const void* keys_in, void* keys_out, const uint32_t* 
       if (a.status_clear_rows < a.num_tiles) a.status_clear_rows = a.num_tiles;
       a.tile_counter = counters + launch;
       a.error = header;
-      a.spin_limit = g_spin_limit;
-      a.fault_tile = g_fault_tile;
+      a.spin_limit = plan.spin_limit;
+      a.fault_tile = plan.fault_tile;
       a.skew_flags = header + kSkewWord + pass;
       a.digit_xor = pass == plan.places - 1 ? signed_top_xor(key_type, begin_bit, end_bit) : 0u;
       if (pass >= 8) {
@@ -448,6 +472,8 @@ struct BatchPlan {
   bool pairs = false;
   int bucket = 0;
   int cfg = 0;  // binning variant
+  int64_t fault_tile = -1;  // test hooks, read once
+  uint32_t spin_limit = 0;
   int places = 0;
   uint32_t tile = 0, small_max = 0;
   uint64_t max_tiles = 0, max_items = 0;
@@ -456,7 +482,7 @@ struct BatchPlan {
 };
 
 int make_batch_plan(int key_type, uint64_t n_total, int64_t num_segments, int value_bytes, int begin_bit,
-                    int end_bit, BatchPlan* bp) {
+                    int end_bit, BatchPlan* bp, int cfg_override = -1) {
   const int kb = key_bits_of(key_type);
   if (kb == 0 || num_segments < 0) return OS_ERR_INVALID_ARG;
   if (value_bytes != 0 && value_bytes != 4) return OS_ERR_INVALID_ARG;
@@ -467,7 +493,10 @@ int make_batch_plan(int key_type, uint64_t n_total, int64_t num_segments, int va
   bp->pairs = value_bytes == 4;
   bp->places = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
   bp->bucket = size_bucket(S > 0 ? n_total / S : n_total);  // by the mean segment length
-  bp->cfg = binning_config(kb, bp->pairs, bp->bucket);
+  if (cfg_override >= kTileConfigs) return OS_ERR_INVALID_ARG;
+  bp->cfg = cfg_override >= 0 ? cfg_override : binning_config(kb, bp->pairs, bp->bucket);
+  bp->fault_tile = g_fault_tile.load(std::memory_order_relaxed);
+  bp->spin_limit = g_spin_limit.load(std::memory_order_relaxed);
   // the persistent kernel serves single arrays: a batch runs geometry 0 with
   // the same ranking
   if (bp->cfg % kGeometries == kPersistentGeometry) bp->cfg -= kPersistentGeometry;
@@ -510,11 +539,11 @@ int make_batch_plan(int key_type, uint64_t n_total, int64_t num_segments, int va
 
 int run_batch(int key_type, const void* keys_in, void* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
               const uint64_t* seg_offsets, int64_t num_segments, uint64_t n_total, int begin_bit, int end_bit,
-              void* ws, size_t ws_bytes, void* stream) {
+              void* ws, size_t ws_bytes, void* stream, int cfg_override = -1) {
   const bool pairs = vals_in != nullptr || vals_out != nullptr;
   if (pairs && (vals_in == nullptr || vals_out == nullptr)) return OS_ERR_INVALID_ARG;
   BatchPlan bp;
-  int rc = make_batch_plan(key_type, n_total, num_segments, pairs ? 4 : 0, begin_bit, end_bit, &bp);
+  int rc = make_batch_plan(key_type, n_total, num_segments, pairs ? 4 : 0, begin_bit, end_bit, &bp, cfg_override);
   if (rc != OS_OK) return rc;
   if (n_total == 0 || num_segments == 0) return OS_OK;
   const size_t kbytes = (size_t)n_total * (bp.key_bits / 8);
@@ -624,8 +653,8 @@ int run_batch(int key_type, const void* keys_in, void* keys_out, const uint32_t*
     a.status_clear_rows = (uint32_t)bp.max_tiles;  // every tile clears its own row
     a.tile_counter = header + kTileCounterWord + pass % 8;
     a.error = header;
-    a.spin_limit = g_spin_limit;
-    a.fault_tile = g_fault_tile;
+    a.spin_limit = bp.spin_limit;
+    a.fault_tile = bp.fault_tile;
     a.seg_offsets = seg_offsets;
     a.tile_base = b.tile_base;
     a.tile_seg = b.tile_seg;
@@ -699,6 +728,43 @@ int os_sort_batch(int key_type, const void* keys_in, void* keys_out, const uint3
                    end_bit, ws, ws_bytes, stream);
 }
 
+// The caller's binning variant (-1: the process-wide one), or an error.
+static int option_config(const os_sort_options* opt, int* cfg) {
+  *cfg = -1;
+  if (!opt) return OS_OK;
+  if (opt->reserved != 0 || opt->tile_config < -1 || opt->tile_config >= kTileConfigs) return OS_ERR_INVALID_ARG;
+  *cfg = opt->tile_config;
+  return OS_OK;
+}
+
+int os_sort_keys_ex(int key_type, const void* keys_in, void* keys_out, uint64_t n, int begin_bit, int end_bit,
+                    void* ws, size_t ws_bytes, void* stream, const os_sort_options* opt) {
+  int cfg;
+  const int rc = option_config(opt, &cfg);
+  if (rc != OS_OK) return rc;
+  return run_sort(key_type, keys_in, keys_out, nullptr, nullptr, n, begin_bit, end_bit, ws, ws_bytes, stream, cfg);
+}
+
+int os_sort_pairs_ex(int key_type, const void* keys_in, void* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
+                     uint64_t n, int begin_bit, int end_bit, void* ws, size_t ws_bytes, void* stream,
+                     const os_sort_options* opt) {
+  if (!vals_in || !vals_out) return OS_ERR_INVALID_ARG;
+  int cfg;
+  const int rc = option_config(opt, &cfg);
+  if (rc != OS_OK) return rc;
+  return run_sort(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws, ws_bytes, stream, cfg);
+}
+
+int os_sort_batch_ex(int key_type, const void* keys_in, void* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
+                     const uint64_t* seg_offsets, int num_segments, uint64_t n_total, int begin_bit, int end_bit,
+                     void* ws, size_t ws_bytes, void* stream, const os_sort_options* opt) {
+  int cfg;
+  const int rc = option_config(opt, &cfg);
+  if (rc != OS_OK) return rc;
+  return run_batch(key_type, keys_in, keys_out, vals_in, vals_out, seg_offsets, num_segments, n_total, begin_bit,
+                   end_bit, ws, ws_bytes, stream, cfg);
+}
+
 int os_digit_histograms(int key_type, const void* keys_in, uint64_t n, int begin_bit, int end_bit,
                         uint32_t* hist_out, uint32_t* offsets_out, void* ws, size_t ws_bytes, void* stream) {
   Plan plan;
@@ -752,6 +818,7 @@ const char* os_status_string(int status) {
 }
 
 int os_profile_start(int capacity) {
+  std::lock_guard<std::mutex> lock(g_prof_mutex);
   if (g_prof || capacity <= 0) return OS_ERR_INVALID_ARG;
   ProfiledLaunch* p = new ProfiledLaunch[capacity];
   for (int i = 0; i < capacity; ++i) {
@@ -768,11 +835,14 @@ int os_profile_start(int capacity) {
   g_prof_capacity = capacity;
   g_prof_used = 0;
   g_prof_seen = 0;
+  g_prof_on.store(true, std::memory_order_release);
   return OS_OK;
 }
 
 int os_profile_stop(os_launch_time* out, int max, int* count) {
+  std::lock_guard<std::mutex> lock(g_prof_mutex);
   if (!g_prof) return OS_ERR_INVALID_ARG;
+  g_prof_on.store(false, std::memory_order_release);
   int rc = OS_OK;
   for (int i = 0; i < g_prof_used; ++i) {
     float ms = 0.f;
@@ -792,6 +862,12 @@ int os_profile_stop(os_launch_time* out, int max, int* count) {
   return rc;
 }
 
+#define OS_STR2(x) #x
+#define OS_STR(x) OS_STR2(x)
+const char* os_build_info(void) { return "cuda_arch_list=" OS_STR(__CUDA_ARCH_LIST__); }
+#undef OS_STR
+#undef OS_STR2
+
 int os_num_tile_configs(void) { return kTileConfigs; }
 
 int os_tile_config_keys(int key_bits, int value_bytes, int cfg) {
@@ -805,13 +881,13 @@ int os_set_tile_config(int key_bits, int value_bytes, int cfg) {
   if ((key_bits != 32 && key_bits != 64) || (value_bytes != 0 && value_bytes != 4) || cfg < 0 ||
       cfg >= kTileConfigs)
     return OS_ERR_INVALID_ARG;
-  for (int b = 0; b < kSizeBuckets; ++b) tile_cfg(key_bits, value_bytes == 4, b) = cfg;
+  for (int b = 0; b < kSizeBuckets; ++b) set_tile_cfg(key_bits, value_bytes == 4, b, cfg);
   return OS_OK;
 }
 
 int os_get_tile_config(int key_bits, int value_bytes) {
   if ((key_bits != 32 && key_bits != 64) || (value_bytes != 0 && value_bytes != 4)) return -1;
-  return tile_cfg(key_bits, value_bytes == 4, kSizeBuckets - 1);
+  return get_tile_cfg(key_bits, value_bytes == 4, kSizeBuckets - 1);
 }
 
 int os_num_size_buckets(void) { return kSizeBuckets; }
@@ -822,7 +898,7 @@ int os_set_tile_config_bucket(int key_bits, int value_bytes, int bucket, int cfg
   if ((key_bits != 32 && key_bits != 64) || (value_bytes != 0 && value_bytes != 4) || cfg < 0 ||
       cfg >= kTileConfigs || bucket < 0 || bucket >= kSizeBuckets)
     return OS_ERR_INVALID_ARG;
-  tile_cfg(key_bits, value_bytes == 4, bucket) = cfg;
+  set_tile_cfg(key_bits, value_bytes == 4, bucket, cfg);
   return OS_OK;
 }
 
@@ -830,18 +906,18 @@ int os_get_tile_config_bucket(int key_bits, int value_bytes, int bucket) {
   if ((key_bits != 32 && key_bits != 64) || (value_bytes != 0 && value_bytes != 4) || bucket < 0 ||
       bucket >= kSizeBuckets)
     return -1;
-  return tile_cfg(key_bits, value_bytes == 4, bucket);
+  return get_tile_cfg(key_bits, value_bytes == 4, bucket);
 }
 
 void os_debug_set_lookback_fault(int64_t tile, uint32_t spin_limit) {
-  g_fault_tile = tile < 0 ? -1 : tile;
-  g_spin_limit = spin_limit == 0 ? kDefaultSpinLimit : spin_limit;
+  g_fault_tile.store(tile < 0 ? -1 : tile, std::memory_order_relaxed);
+  g_spin_limit.store(spin_limit == 0 ? kDefaultSpinLimit : spin_limit, std::memory_order_relaxed);
 }
 
 uint64_t os_debug_set_strip_keys(uint64_t keys) {
   if (keys == 0 || keys > kStripKeys) keys = kStripKeys;
   if (keys < kMinStripKeys) keys = kMinStripKeys;
-  g_strip_keys = keys;
+  g_strip_keys.store(keys, std::memory_order_relaxed);
   return keys;
 }
 

@@ -19,6 +19,7 @@
 //
 // On the way, the grid also zeroes the status-counter slab of the first
 // binning pass, so no separate memset of it is needed.
+#include "../../include/onesweep.h"
 #include "os_common.cuh"
 #include "os_internal.h"
 
@@ -232,3 +233,13 @@ cudaError_t launch_histogram(int key_bits, const HistArgs& a, int num_sms, cudaS
 }
 
 }  // namespace onesweep
+
+// Architecture of the device code in this library as the driver sees it
+// (cudaFuncAttributes::binaryVersion of the histogram kernel, e.g. 103 for
+// sm_103a), or a negative CUDA error code.
+extern "C" OS_API int os_binary_version(void) {
+  cudaFuncAttributes fa{};
+  const cudaError_t e = cudaFuncGetAttributes(&fa, onesweep::histogram_kernel<32, true, false>);
+  return e == cudaSuccess ? fa.binaryVersion : -(int)e;
+}
+

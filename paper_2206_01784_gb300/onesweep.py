@@ -48,6 +48,11 @@ class LaunchTime(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("pass_", ctypes.c_int), ("ms", ctypes.c_float)]
 
 
+class SortOptions(ctypes.Structure):
+    """os_sort_options: the binning variant of one call (-1: process-wide)."""
+    _fields_ = [("tile_config", ctypes.c_int), ("reserved", ctypes.c_uint32)]
+
+
 _lib = None
 
 
@@ -73,6 +78,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.os_sort_batch_workspace_bytes.argtypes = [i32, u64, i32, i32, i32, i32]
     lib.os_sort_batch.restype = i32
     lib.os_sort_batch.argtypes = [i32, vp, vp, vp, vp, vp, i32, u64, i32, i32, vp, sz, vp]
+    opt = ctypes.POINTER(SortOptions)
+    lib.os_sort_keys_ex.restype = i32
+    lib.os_sort_keys_ex.argtypes = [i32, vp, vp, u64, i32, i32, vp, sz, vp, opt]
+    lib.os_sort_pairs_ex.restype = i32
+    lib.os_sort_pairs_ex.argtypes = [i32, vp, vp, vp, vp, u64, i32, i32, vp, sz, vp, opt]
+    lib.os_sort_batch_ex.restype = i32
+    lib.os_sort_batch_ex.argtypes = [i32, vp, vp, vp, vp, vp, i32, u64, i32, i32, vp, sz, vp, opt]
     lib.os_sort_noalloc.restype = i32
     lib.os_sort_noalloc.argtypes = [i32, vp, vp, vp, vp, u64, i32, i32, vp, ctypes.POINTER(ctypes.c_void_p)]
     lib.os_digit_histograms.restype = i32
@@ -81,6 +93,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.os_workspace_status.argtypes = [vp, vp]
     lib.os_status_string.restype = ctypes.c_char_p
     lib.os_status_string.argtypes = [i32]
+    lib.os_build_info.restype = ctypes.c_char_p
+    lib.os_build_info.argtypes = []
+    lib.os_binary_version.restype = i32
+    lib.os_binary_version.argtypes = []
     lib.os_debug_set_lookback_fault.restype = None
     lib.os_debug_set_lookback_fault.argtypes = [i64, u32]
     lib.os_debug_set_strip_keys.restype = u64
@@ -148,6 +164,28 @@ def os_sort_pairs(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, 
                                     ws_bytes, stream))
 
 
+def _options(tile_config):
+    return None if tile_config is None else ctypes.byref(SortOptions(int(tile_config), 0))
+
+
+def os_sort_keys_ex(key_type, keys_in, keys_out, n, begin_bit, end_bit, ws, ws_bytes, stream,
+                    tile_config=None) -> int:
+    return int(load().os_sort_keys_ex(key_type, keys_in, keys_out, n, begin_bit, end_bit, ws, ws_bytes, stream,
+                                      _options(tile_config)))
+
+
+def os_sort_pairs_ex(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws, ws_bytes, stream,
+                     tile_config=None) -> int:
+    return int(load().os_sort_pairs_ex(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws,
+                                       ws_bytes, stream, _options(tile_config)))
+
+
+def os_sort_batch_ex(key_type, keys_in, keys_out, vals_in, vals_out, seg_offsets, num_segments, n_total, begin_bit,
+                     end_bit, ws, ws_bytes, stream, tile_config=None) -> int:
+    return int(load().os_sort_batch_ex(key_type, keys_in, keys_out, vals_in, vals_out, seg_offsets, num_segments,
+                                       n_total, begin_bit, end_bit, ws, ws_bytes, stream, _options(tile_config)))
+
+
 def os_sort_batch_workspace_bytes(key_type: int, n_total: int, num_segments: int, value_bytes: int, begin_bit: int,
                                   end_bit: int) -> int:
     return int(load().os_sort_batch_workspace_bytes(key_type, n_total, num_segments, value_bytes, begin_bit, end_bit))
@@ -206,6 +244,14 @@ def os_sort_pairs_host(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_
                        stream) -> int:
     return int(load().os_sort_pairs_host(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws,
                                          ws_bytes, stream))
+
+
+def os_build_info() -> str:
+    return load().os_build_info().decode()
+
+
+def os_binary_version() -> int:
+    return int(load().os_binary_version())
 
 
 def os_num_tile_configs() -> int:

@@ -38,10 +38,9 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_library_built_for_sm103a():
-    out = subprocess.run(["cuobjdump", "--list-elf", osw.LIB_PATH], capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    assert "sm_103a" in out.stdout
+    # the compile-time architecture list of the device code (no GPU needed);
+    # the GPU tests check the loaded code's binary version as well
+    assert osw.os_build_info() == "cuda_arch_list=1030"
 
 
 def test_workspace_sizes():

@@ -67,6 +67,11 @@ def make_keys(kt, dist, n, seed):
     return workload.keys(kt, dist, n, seed)
 
 
+def test_loaded_device_code_is_sm103():
+    _dev()
+    assert osw.os_binary_version() == 103
+
+
 # ---------------------------------------------------------------- phase 1 + 2
 
 @pytest.mark.parametrize("kt,begin,end", [("u32", 0, 32), ("u32", 3, 29), ("u64", 0, 64), ("u64", 5, 50),

@@ -4,10 +4,12 @@ Such callers (code whose device memory belongs to another allocator, or that
 must not trigger the implicit device synchronization of cudaMalloc/cudaFree)
 hand over only their inputs and outputs; the scratch comes from a fixed
 16 MiB array of static device memory in the library. These tests call the
-entry point through the C ABI twice in a row on different inputs and require
-the output of each call to equal the regular entry point's (os_sort_pairs /
-os_sort_keys, which take a caller-allocated workspace) bit for bit. They also
-check that a sort too large for the fixed scratch is refused.
+entry point through the C ABI twice in a row on different inputs (the second
+call finds the first one's leftovers in the shared scratch) and require the
+output of each call to equal, bit for bit, both the regular entry point's
+(os_sort_pairs / os_sort_keys, which take a caller-allocated workspace) and
+the CPU oracle's. They also check that a sort too large for the fixed
+scratch is refused, and that argument errors are named first.
 
 This file is collected last so that, if it fails, a run stopping at the first
 failure has already run every other test. It passes alone in a fresh process
@@ -18,6 +20,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle  # noqa: E402
 from paper_2206_01784_gb300 import onesweep as osw  # noqa: E402
 from paper_2206_01784_gb300 import workload  # noqa: E402
 
@@ -87,6 +90,15 @@ def test_noalloc_matches_regular_entry_point_twice(kt, pairs, n, begin, end):
         assert torch.equal(nk, rk), (kt, n, call)
         if pairs:
             assert torch.equal(nv, rv), (kt, n, call)
+        # and element by element against the CPU oracle
+        kd = np.uint64 if keys.dtype.itemsize == 8 else np.uint32
+        got_k = nk.cpu().numpy().view(kd)
+        if pairs:
+            ek, ev = oracle.sort(kt, keys, workload.iota_u32(n), begin, end)
+            assert np.array_equal(got_k, ek), (kt, n, call)
+            assert np.array_equal(nv.cpu().numpy().view(np.uint32), ev), (kt, n, call)
+        else:
+            assert np.array_equal(got_k, oracle.sort(kt, keys, None, begin, end)), (kt, n, call)
 
 
 def test_noalloc_rejects_sorts_beyond_its_scratch():
@@ -99,6 +111,9 @@ def test_noalloc_rejects_sorts_beyond_its_scratch():
     rc, _ = osw.os_sort_noalloc(osw.OS_KEY_U32, k.data_ptr(), ko.data_ptr(), v.data_ptr(), vo.data_ptr(), n, 0, 32, s)
     assert rc == osw.OS_ERR_SCRATCH_LIMIT
     assert "16 MiB" in osw.os_status_string(rc)
-    # argument errors are still named as by the regular entry point
+    # argument errors are still named as by the regular entry point, before
+    # the scratch limit: a bad bit range, one value pointer without the other
     rc, _ = osw.os_sort_noalloc(osw.OS_KEY_U32, k.data_ptr(), ko.data_ptr(), None, None, 1000, 0, 33, s)
+    assert rc == osw.OS_ERR_INVALID_ARG
+    rc, _ = osw.os_sort_noalloc(osw.OS_KEY_U32, k.data_ptr(), ko.data_ptr(), v.data_ptr(), None, n, 0, 32, s)
     assert rc == osw.OS_ERR_INVALID_ARG
