@@ -72,6 +72,16 @@ typedef enum {
     OS_KEY_I64 = 5
 } os_key_type;
 
+/*
+ * OR'd into any key_type argument: stable descending order - keys from the
+ * largest sorted-on field down, equal keys still in their input order. The
+ * paper sorts ascending only (Section 4); each digit place here bins by the
+ * complement of its digit within the place, which costs nothing (the same
+ * XOR that orders signed keys). For float keys, +0.0 comes before -0.0 and
+ * NaNs follow their bit patterns, reversed.
+ */
+#define OS_SORT_DESCENDING 0x100
+
 typedef enum {
     OS_OK = 0,
     OS_ERR_INVALID_ARG = 1, /* bad key type, bit range, pointer, alignment or overlap */

@@ -165,8 +165,13 @@ void prof_end(int slot, cudaStream_t s) {
 
 size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
+// key_type is a key type, optionally with OS_SORT_DESCENDING OR'd in.
+bool known_flags(int key_type) { return (key_type & ~0xFF & ~OS_SORT_DESCENDING) == 0; }
+bool is_descending(int key_type) { return (key_type & OS_SORT_DESCENDING) != 0; }
+
 int key_bits_of(int key_type) {
-  switch (key_type) {
+  if (!known_flags(key_type)) return 0;
+  switch (key_type & 0xFF) {
     case OS_KEY_U32:
     case OS_KEY_F32:
     case OS_KEY_I32: return 32;
@@ -177,7 +182,7 @@ int key_bits_of(int key_type) {
   }
 }
 
-bool is_float(int key_type) { return key_type == OS_KEY_F32 || key_type == OS_KEY_F64; }
+bool is_float(int key_type) { return (key_type & 0xFF) == OS_KEY_F32 || (key_type & 0xFF) == OS_KEY_F64; }
 
 // Signed keys sort as their bits with the sign bit inverted (two's complement
 // order). Only the most significant place holds the sign bit, so instead of
@@ -185,7 +190,8 @@ bool is_float(int key_type) { return key_type == OS_KEY_F32 || key_type == OS_KE
 // sorted range reaches the sign bit.
 uint32_t signed_top_xor(int key_type, int begin_bit, int end_bit) {
   const int kb = key_bits_of(key_type);
-  if ((key_type != OS_KEY_I32 && key_type != OS_KEY_I64) || end_bit != kb || end_bit <= begin_bit) return 0u;
+  const int base = key_type & 0xFF;
+  if ((base != OS_KEY_I32 && base != OS_KEY_I64) || end_bit != kb || end_bit <= begin_bit) return 0u;
   const int places = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
   const int top_width = end_bit - (begin_bit + kRadixBits * (places - 1));
   return 1u << (top_width - 1);
@@ -325,6 +331,7 @@ int run_histogram(const Plan& plan, int key_type, const void* keys, uint64_t n, 
   h.clear_words = clear_slab0 ? first_tiles * kRadix : 0;
   h.skew = reinterpret_cast<uint32_t*>(ws) + kSkewWord;
   h.top_xor = signed_top_xor(key_type, begin_bit, end_bit);
+  h.descending = is_descending(key_type) ? 1u : 0u;
   const int sms = device_sm_count();
   if (sms <= 0) return OS_ERR_CUDA;
   const int slot = prof_begin(0, -1, s);
@@ -440,7 +447,10 @@ int run_sort(int key_type, const void* keys_in, void* keys_out, const uint32_t* 
       a.spin_limit = plan.spin_limit;
       a.fault_tile = plan.fault_tile;
       a.skew_flags = header + kSkewWord + pass;
-      a.digit_xor = pass == plan.places - 1 ? signed_top_xor(key_type, begin_bit, end_bit) : 0u;
+      // signed keys: the top place's high digit bit inverted; descending:
+      // every digit complemented within its place
+      a.digit_xor = (pass == plan.places - 1 ? signed_top_xor(key_type, begin_bit, end_bit) : 0u) ^
+                    (is_descending(key_type) ? a.mask : 0u);
       if (pass >= 8) {
         // more than 8 passes cannot happen with 8-bit digits of <= 64-bit keys
         return OS_ERR_INVALID_ARG;
@@ -607,6 +617,7 @@ int run_batch(int key_type, const void* keys_in, void* keys_out, const uint32_t*
   b.seg_bin_offsets = reinterpret_cast<uint32_t*>(w + bp.seg_bin_offsets);
   b.seg_skew = reinterpret_cast<uint32_t*>(w + bp.seg_skew);
   b.top_xor = signed_top_xor(key_type, begin_bit, end_bit);
+  b.descending = is_descending(key_type) ? 1u : 0u;
   b.error = header;
   b.clear = reinterpret_cast<uint32_t*>(w + bp.status[0]);
   b.clear_words = bp.max_tiles * kRadix;
@@ -661,7 +672,7 @@ int run_batch(int key_type, const void* keys_in, void* keys_out, const uint32_t*
     a.total_tiles = b.totals;
     a.skew_flags = b.seg_skew + pass;
     a.skew_stride = (uint32_t)bp.places;
-    a.digit_xor = pass == bp.places - 1 ? b.top_xor : 0u;
+    a.digit_xor = (pass == bp.places - 1 ? b.top_xor : 0u) ^ (b.descending ? a.mask : 0u);
     slot = prof_begin(1, pass, s);
     e = launch_binning(bp.key_bits, pairs, bp.cfg, a, s);
     prof_end(slot, s);

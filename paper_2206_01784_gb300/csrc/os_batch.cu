@@ -158,7 +158,10 @@ __global__ void __launch_bounds__(kSegHistThreads) batch_histogram_kernel(BatchA
   __threadfence();
   uint32_t* go = b.seg_bin_offsets + (size_t)seg * p * kRadix;
   for (int pl = 0; pl < p; ++pl) {
-    const uint32_t c = tid < kRadix ? ld_relaxed_gpu(gh + pl * kRadix + tid) : 0u;
+    // descending: bins of the complemented digits (count of t = count of t ^ mask)
+    const uint32_t pmask = pl == p - 1 ? last_mask : 0xFFu;
+    const uint32_t src = b.descending ? (tid ^ pmask) : (uint32_t)tid;
+    const uint32_t c = (tid < kRadix && (uint32_t)tid <= pmask) ? ld_relaxed_gpu(gh + pl * kRadix + src) : 0u;
     const uint32_t excl = block_exclusive_sum<kSegHistThreads>(c, scan_tmp);
     if (tid < kRadix) go[pl * kRadix + tid] = excl;
     const int skewed = __syncthreads_or(tid < kRadix && (uint64_t)c * 16u > len);
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(LocalConfig<KBITS>::NT) batch_local_sort_kerne
     const int shift = b.begin_bit + 8 * pass;
     const int width = min(8, b.end_bit - shift);
     const uint32_t mask = (1u << width) - 1u;
-    const uint32_t dxor = pass == b.num_places - 1 ? b.top_xor : 0u;
+    const uint32_t dxor = (pass == b.num_places - 1 ? b.top_xor : 0u) ^ (b.descending ? mask : 0u);
     for (int i = tid; i < 2 * NW * kRadix; i += NT) whist[i] = 0;
     __syncthreads();  // staged keys (or the previous pass's scatter) visible
     K key[IPT];

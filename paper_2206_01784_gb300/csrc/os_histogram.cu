@@ -183,9 +183,15 @@ __global__ void __launch_bounds__(kHistThreads, 1) histogram_kernel(HistArgs a) 
   if (!s_last) return;
   __threadfence();
   for (int pl = 0; pl < p; ++pl) {
-    const uint32_t c = tid < kRadix ? ld_relaxed_gpu(a.hist + pl * kRadix + tid) : 0u;
+    // a descending sort bins by the complement of each digit within its
+    // place: count of complemented digit t = count of digit t ^ mask
+    const uint32_t pmask = pl == p - 1 ? last_mask : 0xFFu;
+    const uint32_t src = a.descending ? (tid ^ pmask) : (uint32_t)tid;
+    const uint32_t c = (tid < kRadix && (uint32_t)tid <= pmask) ? ld_relaxed_gpu(a.hist + pl * kRadix + src) : 0u;
     const uint32_t excl = block_exclusive_sum<kHistThreads>(c, scan_tmp);
     if (tid < kRadix) a.offsets[pl * kRadix + tid] = excl;
+    // (every read of this place's counts is before the scan's barriers)
+    if (a.descending && tid < kRadix) a.hist[pl * kRadix + tid] = c;
     // a place where one digit holds over 1/16 of the keys is "skewed": its
     // binning pass ranks with ballots, which do not slow down when many lanes
     // share a digit

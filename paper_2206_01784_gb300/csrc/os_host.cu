@@ -21,7 +21,7 @@ struct HostLayout {
 };
 
 int key_bytes_of(int key_type) {
-  switch (key_type) {
+  switch (key_type & 0xFF) {  // OS_SORT_DESCENDING may be OR'd in
     case OS_KEY_U32:
     case OS_KEY_F32:
     case OS_KEY_I32: return 4;

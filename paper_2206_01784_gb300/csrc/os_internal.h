@@ -23,6 +23,7 @@ struct HistArgs {
   uint64_t clear_words;
   uint32_t* skew;            // [p] set to 1 where one digit holds over 1/16 of the keys (may be null)
   uint32_t top_xor;          // signed keys: high bit of the top place's digit inverted (else 0)
+  uint32_t descending;       // offsets (and the reported histograms) for complemented digits
 };
 
 // Phase 3, one digit-binning pass (Section 3, "Chained scan digit-binning kernel").
@@ -101,6 +102,7 @@ struct BatchArgs {
   uint32_t* seg_bin_offsets;     // [S][p][256]
   uint32_t* seg_skew;            // [S][p] skewed-place flags
   uint32_t top_xor;              // signed keys: high bit of the top place's digit inverted (else 0)
+  uint32_t descending;           // bin by the complemented digit of every place
   uint32_t* error;
   uint32_t* clear;               // status slab of the first pass, to zero
   uint64_t clear_words;

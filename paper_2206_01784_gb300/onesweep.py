@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libonesweep.so")
 
 OS_KEY_U32, OS_KEY_U64, OS_KEY_F32, OS_KEY_F64, OS_KEY_I32, OS_KEY_I64 = 0, 1, 2, 3, 4, 5
+OS_SORT_DESCENDING = 0x100  # OR into a key type: stable descending order
 KEY_TYPES = {"u32": OS_KEY_U32, "u64": OS_KEY_U64, "f32": OS_KEY_F32, "f64": OS_KEY_F64, "i32": OS_KEY_I32,
              "i64": OS_KEY_I64}
 KEY_BITS = {OS_KEY_U32: 32, OS_KEY_U64: 64, OS_KEY_F32: 32, OS_KEY_F64: 64, OS_KEY_I32: 32, OS_KEY_I64: 64}
@@ -362,12 +363,17 @@ def _check(rc: int, where: str):
         raise OnesweepError(rc, where)
 
 
+def _with_order(kt: int, descending: bool) -> int:
+    return kt | OS_SORT_DESCENDING if descending else kt
+
+
 def sort_keys(keys, begin_bit: int = 0, end_bit: int | None = None, key_type=None, out=None, ws=None,
-              stream=None):
-    """Stable ascending sort of a 1-D CUDA tensor of keys; returns the sorted keys."""
+              stream=None, descending: bool = False):
+    """Stable ascending (or descending) sort of a 1-D CUDA tensor of keys; returns the sorted keys."""
     torch = _torch()
     kt = key_type_of(keys, key_type)
     end_bit = KEY_BITS[kt] if end_bit is None else end_bit
+    kt = _with_order(kt, descending)
     keys = keys.contiguous()
     n = keys.numel()
     out = torch.empty_like(keys) if out is None else out
@@ -378,11 +384,12 @@ def sort_keys(keys, begin_bit: int = 0, end_bit: int | None = None, key_type=Non
 
 
 def sort_pairs(keys, values, begin_bit: int = 0, end_bit: int | None = None, key_type=None, keys_out=None,
-               values_out=None, ws=None, stream=None):
-    """Stable ascending sort of (key, uint32 value) pairs; returns (keys, values)."""
+               values_out=None, ws=None, stream=None, descending: bool = False):
+    """Stable ascending (or descending) sort of (key, uint32 value) pairs; returns (keys, values)."""
     torch = _torch()
     kt = key_type_of(keys, key_type)
     end_bit = KEY_BITS[kt] if end_bit is None else end_bit
+    kt = _with_order(kt, descending)
     keys = keys.contiguous()
     values = values.contiguous()
     if values.element_size() != 4 or values.numel() != keys.numel():
@@ -397,7 +404,7 @@ def sort_pairs(keys, values, begin_bit: int = 0, end_bit: int | None = None, key
 
 
 def sort_host(keys, values=None, begin_bit: int = 0, end_bit: int | None = None, key_type=None, device=None,
-              stream=None):
+              stream=None, descending: bool = False):
     """Stable ascending sort of keys (and uint32 values) held in host memory:
     1-D CPU tensors (pinned ones copy asynchronously) or numpy arrays. One
     os_sort_keys_host / os_sort_pairs_host call uploads, sorts on the GPU and
@@ -411,6 +418,7 @@ def sort_host(keys, values=None, begin_bit: int = 0, end_bit: int | None = None,
     kt = KEY_TYPES[key_type] if isinstance(key_type, str) else (
         int(key_type) if key_type is not None else _host_key_type(k))
     end_bit = KEY_BITS[kt] if end_bit is None else end_bit
+    kt = _with_order(kt, descending)
     n = k.numel()
     ko = torch.empty_like(k, pin_memory=k.is_pinned())
     v = vo = None
@@ -449,11 +457,15 @@ def _host_key_type(t) -> int:
     raise TypeError(f"unsupported key dtype {t.dtype}")
 
 
-def digit_histograms(keys, begin_bit: int = 0, end_bit: int | None = None, key_type=None, stream=None):
-    """Digit counts and global bin offsets of every place: two int32 tensors [p, 256]."""
+def digit_histograms(keys, begin_bit: int = 0, end_bit: int | None = None, key_type=None, stream=None,
+                     descending: bool = False):
+    """Digit counts and global bin offsets of every place: two int32 tensors
+    [p, 256] (of the complemented digits a descending sort bins by, when
+    descending)."""
     torch = _torch()
     kt = key_type_of(keys, key_type)
     end_bit = KEY_BITS[kt] if end_bit is None else end_bit
+    kt = _with_order(kt, descending)
     keys = keys.contiguous()
     n = keys.numel()
     p = (end_bit - begin_bit + 7) // 8
@@ -475,13 +487,14 @@ def batch_workspace(key_type: int, n_total: int, num_segments: int, value_bytes:
 
 
 def sort_batch(keys, seg_offsets, values=None, begin_bit: int = 0, end_bit: int | None = None, key_type=None,
-               keys_out=None, values_out=None, ws=None, stream=None):
+               keys_out=None, values_out=None, ws=None, stream=None, descending: bool = False):
     """Sorts each segment [seg_offsets[s], seg_offsets[s+1]) of a 1-D CUDA
     tensor on its own. seg_offsets: int64 CUDA tensor of num_segments + 1
     boundaries. Returns keys (or (keys, values))."""
     torch = _torch()
     kt = key_type_of(keys, key_type)
     end_bit = KEY_BITS[kt] if end_bit is None else end_bit
+    kt = _with_order(kt, descending)
     keys = keys.contiguous()
     offs = seg_offsets.contiguous()
     if offs.dtype not in (torch.int64, torch.uint64) or offs.device != keys.device:
