@@ -54,6 +54,8 @@ def parse_args():
     p.add_argument("--keys-only", action="store_true", help="sort keys without values")
     p.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
     p.add_argument("--serve-requests", type=int, default=10000)
+    p.add_argument("--no-std-full", action="store_true",
+                   help="time std::stable_sort on 2^24 pairs only (not on the whole workload)")
     p.add_argument("--tile-config", type=int, default=None,
                    help="binning variant for the timed sorts (os_set_tile_config; default: the library's choice)")
     args = p.parse_args()
@@ -214,6 +216,128 @@ def time_oracle(n: int, dist: str, seed: int, repeats: int = 1, key_type: str = 
     return times
 
 
+def time_cpu_baselines(keys_np, vals_np, key_type: str, full_std: bool = True):
+    """The CPU comparison rows on this host (not the oracle; checked against it
+    by tests/test_cpu_baselines.py): the multi-threaded LSD radix sort on all
+    host threads over the whole workload, and std::stable_sort on one thread
+    over its first 2^24 pairs and (full_std) the whole workload."""
+    import oracle
+
+    n = keys_np.size
+    threads = oracle.hardware_threads()
+    t0 = time.perf_counter()
+    oracle.parallel_sort(key_type, keys_np, vals_np, threads=threads)
+    t_par = time.perf_counter() - t0
+    rows = {"parallel_lsd": {"value": n / t_par / 1e9, "unit": UNIT, "threads": threads, "seconds": t_par,
+                             "sample": f"the whole workload ({n} pairs), 8-bit places, all host threads"}}
+    std = {}
+    sizes = [min(n, 1 << 24)] + ([n] if full_std and n > (1 << 24) else [])
+    for m in sizes:
+        t0 = time.perf_counter()
+        oracle.std_stable_sort(key_type, keys_np[:m], vals_np[:m])
+        dt = time.perf_counter() - t0
+        std[f"n={m}"] = {"value": m / dt / 1e9, "unit": UNIT, "seconds": dt, "threads": 1}
+    rows["std_stable_sort"] = std
+    return rows
+
+
+def measure_config(torch, osw, workload, np, dev, key_type: str, log2n: int, pairs: bool, dist: str, seed: int,
+                   steps: int = 10, warmup: int = 3):
+    """One more workload configuration through os_sort_pairs / os_sort_keys,
+    timed like the headline (CUDA events around the steps, launch times from
+    the library's profile hooks): GKeys/s, ms per step, the binning kernel's
+    and the whole step's fraction of the HBM roofline."""
+    n = 1 << log2n
+    bits = KEY_BITS[key_type]
+    kbytes = bits // 8
+    kview = np.int64 if bits == 64 else np.int32
+    keys = torch.from_numpy(workload.keys(key_type, dist, n, seed).view(kview)).to(dev)
+    vals = torch.from_numpy(workload.iota_u32(n).view(np.int32)).to(dev) if pairs else None
+    ko = torch.empty_like(keys)
+    vo = torch.empty_like(vals) if pairs else None
+    kt = osw.KEY_TYPES[key_type]
+    lay = osw.os_sort_workspace_layout(kt, n, 4 if pairs else 0, 0, bits)
+    ws = torch.empty(lay.total_bytes, dtype=torch.uint8, device=dev)
+    sp = torch.cuda.current_stream(dev).cuda_stream
+
+    def step():
+        if pairs:
+            rc = osw.os_sort_pairs(kt, keys.data_ptr(), ko.data_ptr(), vals.data_ptr(), vo.data_ptr(), n, 0, bits,
+                                   ws.data_ptr(), ws.numel(), sp)
+        else:
+            rc = osw.os_sort_keys(kt, keys.data_ptr(), ko.data_ptr(), n, 0, bits, ws.data_ptr(), ws.numel(), sp)
+        if rc != osw.OS_OK:
+            raise osw.OnesweepError(rc, "sort")
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    cap = steps * (lay.num_places + 1) + 16
+    osw.os_profile_start(cap)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    _, _, recs = osw.os_profile_stop(cap)
+    if osw.os_workspace_status(ws.data_ptr(), sp) != osw.OS_OK:
+        raise RuntimeError("device status after the configuration's steps")
+    ok64 = order_key(torch, ko, key_type)
+    if not bool((ok64[1:] >= ok64[:-1]).all().item()):
+        raise RuntimeError("configuration output not sorted")
+    peak, _ = hbm_peak()
+    bin_ms = statistics.mean([m for k, _, m in recs if k == 1])
+    per_pass = n * 2 * (kbytes + (4 if pairs else 0))
+    step_bytes = n * kbytes + lay.num_places * per_pass
+    return {"workload": workload_name(n, dist, seed, pairs, key_type), "keys": n, "places": lay.num_places,
+            "gkeys_per_s": n / ms / 1e6, "ms_per_step": ms, "binning_avg_ms": bin_ms,
+            "binning_frac": per_pass / (bin_ms / 1e3) / 1e9 / peak,
+            "step_frac": step_bytes / (ms / 1e3) / 1e9 / peak, "steps": steps}
+
+
+def measure_copy_ceiling(torch, dev, nbytes: int):
+    """Plain cudaMemcpyAsync rates between pinned host memory and the device
+    on this machine: host-to-device, device-to-host, and both at once on two
+    streams (GB/s) - the ceiling for an end-to-end sort that moves its inputs
+    up and its result down."""
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h2 = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d2 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize(dev)
+        return (time.perf_counter() - t0) / reps
+
+    def up():
+        with torch.cuda.stream(s1):
+            d.copy_(h, non_blocking=True)
+
+    def down():
+        with torch.cuda.stream(s1):
+            h.copy_(d, non_blocking=True)
+
+    def both():
+        with torch.cuda.stream(s1):
+            d.copy_(h, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h2.copy_(d2, non_blocking=True)
+
+    t_up, t_down, t_both = timed(up), timed(down), timed(both)
+    return {"h2d_gbs": nbytes / t_up / 1e9, "d2h_gbs": nbytes / t_down / 1e9,
+            "both_directions_gbs_each": nbytes / t_both / 1e9, "bytes_per_copy": nbytes,
+            "api": "cudaMemcpyAsync (torch copy_) from/to pinned host memory"}
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle timed on the host cores, rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
@@ -308,36 +432,45 @@ def measure_batch(torch, osw, workload, np, dev, steps: int = 20):
 def measure_serving(torch, dev, count: int, sweep_loads=()):
     """Continuous batching of a Poisson request stream (sizes log-uniform
     16K-64M keys, key types 60/25/15 % u32/u64/f32 with u32 values, 40 GB
-    device budget, seed 11): capacity first (every request present at once),
-    then the offered load at 0.7x that capacity in real time; p50/p99 latency
-    from arrival to completion."""
+    device budget, seed 11), two ways: request data copied from pinned host
+    memory per request (the service the host link bounds), and request data
+    already in device memory (the service the sorts bound). For each: the
+    capacity (every request present at once), then the stream offered in real
+    time at 0.7x that capacity and at the sweep's other loads; p50/p99 latency
+    from arrival to completion and requests per batch at every load."""
     from paper_2206_01784_gb300 import serve
 
-    srv = serve.Server(budget_bytes=40 * 10**9, device=dev)
-    probe = serve.make_requests(count, seed=11, rate_per_s=1.0)
-    for r in probe:
-        r.arrival = 0.0
-    cap = srv.run(probe, realtime=False)
-    mean_keys = sum(r.n for r in probe) / len(probe)
-    capacity_rps = cap["gkeys_per_s"] * 1e9 / mean_keys
-    reqs = serve.make_requests(count, seed=11, rate_per_s=0.7 * capacity_rps)
-    st = srv.run(reqs, realtime=True)
-    # the same stream offered at other fractions of the capacity
-    sweep = []
-    for load in sweep_loads:
-        sw = srv.run(serve.make_requests(count, seed=11, rate_per_s=load * capacity_rps), realtime=True)
-        sweep.append({"load": load, "gkeys_per_s": sw["gkeys_per_s"], "p50_ms": sw["p50_ms"], "p99_ms": sw["p99_ms"],
-                      "tail_wait_ms": sw["tail_wait_ms"], "tail_service_ms": sw["tail_service_ms"],
-                      "mean_batch_requests": sw["mean_batch_requests"]})
-    return {"workload": f"{count} requests, Poisson arrivals at 0.7x measured capacity, sizes log-uniform 16K-64M, "
-                        "u32/u64/f32 keys 60/25/15 % + u32 values, 40 GB budget, inputs copied from pinned host "
-                        "memory, seed 11",
-            "capacity_gkeys_per_s": cap["gkeys_per_s"], "offered_requests_per_s": 0.7 * capacity_rps,
-            "gkeys_per_s": st["gkeys_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-            "tail_wait_ms": st["tail_wait_ms"], "tail_service_ms": st["tail_service_ms"],
-            "tail_mean_keys": st["tail_mean_keys"],
-            "mean_ms": st["mean_ms"], "batches": st["batches"], "mean_batch_requests": st["mean_batch_requests"],
-            "keys": st["keys"], "load_sweep": sweep}
+    def one(resident: bool):
+        srv = serve.Server(budget_bytes=40 * 10**9, device=dev, device_resident=resident)
+        probe = serve.make_requests(count, seed=11, rate_per_s=1.0)
+        for r in probe:
+            r.arrival = 0.0
+        cap = srv.run(probe, realtime=False)
+        mean_keys = sum(r.n for r in probe) / len(probe)
+        capacity_rps = cap["gkeys_per_s"] * 1e9 / mean_keys
+        out = {"capacity_gkeys_per_s": cap["gkeys_per_s"], "capacity_mean_batch_requests": cap["mean_batch_requests"]}
+        loads = []
+        for load in (0.7,) + tuple(sweep_loads):
+            st = srv.run(serve.make_requests(count, seed=11, rate_per_s=load * capacity_rps), realtime=True)
+            loads.append({"load": load, "offered_requests_per_s": load * capacity_rps, "gkeys_per_s": st["gkeys_per_s"],
+                          "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+                          "tail_wait_ms": st["tail_wait_ms"], "tail_service_ms": st["tail_service_ms"],
+                          "batches": st["batches"], "mean_batch_requests": st["mean_batch_requests"]})
+        out["loads"] = loads
+        del srv
+        torch.cuda.empty_cache()
+        return out
+
+    host = one(False)
+    resident = one(True)
+    at07 = host["loads"][0]
+    return {"workload": f"{count} requests, Poisson arrivals, sizes log-uniform 16K-64M, u32/u64/f32 keys 60/25/15 % "
+                        "+ u32 values, 40 GB budget, seed 11; offered at 0.7x (and the sweep's loads) of each "
+                        "service's measured capacity",
+            # the headline service (inputs copied from pinned host memory), as before
+            "capacity_gkeys_per_s": host["capacity_gkeys_per_s"], "gkeys_per_s": at07["gkeys_per_s"],
+            "p50_ms": at07["p50_ms"], "p99_ms": at07["p99_ms"], "mean_batch_requests": at07["mean_batch_requests"],
+            "host_inputs": host, "device_resident": resident}
 
 
 def main():
@@ -523,8 +656,19 @@ def main():
         if not ok:
             raise RuntimeError("end-to-end result differs from the device result")
 
-    batched = serving = None
+    batched = serving = configs = copy_ceiling = None
     if world == 1 and not args.no_extras:
+        # the other workload configurations at full size (extras, not the headline)
+        configs = {}
+        for name, kt_, log2n_, pairs_, dist_, seed_ in (("keys_only_256m_u32", "u32", 28, False, "uniform", 1),
+                                                        ("u64_pairs_128m", "u64", 27, True, "uniform", 8),
+                                                        ("f32_pairs_256m", "f32", 28, True, "normal", 9)):
+            configs[name] = measure_config(torch, osw, workload, np, dev, kt_, log2n_, pairs_, dist_, seed_)
+            torch.cuda.empty_cache()
+        copy_ceiling = measure_copy_ceiling(torch, dev, n * (kbytes + (4 if pairs else 0)))
+        if e2e is not None:
+            moved = e2e["h2d_bytes_per_step"] + e2e["d2h_bytes_per_step"]
+            copy_ceiling["e2e_bound_gkeys_per_s"] = n / (moved / 2 / (copy_ceiling["both_directions_gbs_each"] * 1e9)) / 1e9
         batched = measure_batch(torch, osw, workload, np, dev)
         if args.serve_requests > 0:
             loads = [float(x) for x in args.serve_sweep.split(",") if x.strip()]
@@ -537,6 +681,8 @@ def main():
         cpu = {"value": sample / times[0] / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{sample} {args.key_type} pairs (half the workload, same distribution), single-threaded C oracle, "
                          f"{times[0]:.1f} s", "cpu": cpu_model(), "nproc": os.cpu_count()}
+        # comparison rows on the same host cores (not the oracle)
+        cpu.update(time_cpu_baselines(keys_np, vals_np, args.key_type, full_std=not args.no_std_full))
 
     if rank == 0:
         line = {
@@ -550,7 +696,7 @@ def main():
                              "larger than L2"},
             "roofline": roofline, "roofline_step": step_roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "gpu": torch.cuda.get_device_name(dev),
-            "batched": batched, "serving": serving,
+            "batched": batched, "serving": serving, "configs": configs, "copy_ceiling": copy_ceiling,
             "paper_context": "A100-80GB: 29.4 GKey/s, 256M u32 keys only (different hardware and workload)",
         }
         print(json.dumps(line), flush=True)

@@ -9,6 +9,12 @@ The arithmetic lives in ``onesweep_oracle.c`` (plain C, one key at a time,
 module only marshals numpy arrays. ``lookback_sim`` holds a pure-Python model
 of the chained-scan status-counter protocol for small cases.
 
+``cpu_baselines.cpp`` (``libcpu_baselines.so``) is not the oracle: it holds
+the benchmark's CPU comparison rows, a multi-threaded LSD radix sort and
+std::stable_sort, each checked bit for bit against the oracle
+(``tests/test_cpu_baselines.py``); ``parallel_sort`` and ``std_stable_sort``
+call them.
+
 Pins (checked in ``tests/test_oracle.py`` without a GPU):
   * exclusive sum: the paper's worked example (Section 2), golden fixture;
   * one binning pass: the paper's flag prefix-sum example (Section 2);
@@ -35,13 +41,69 @@ KEY_TYPES = {"u32": 0, "u64": 1, "f32": 2, "f64": 3, "i32": 4, "i64": 5}
 RADIX_BITS = 8
 
 
+_CPB_SRC = os.path.join(_HERE, "cpu_baselines.cpp")
+_CPB_PATH = os.path.join(_HERE, "libcpu_baselines.so")
+_cpb = None
+
+
 def build(force: bool = False) -> str:
-    """Compile the C oracle with gcc (no CUDA involved)."""
+    """Compile the C oracle with gcc (no CUDA involved), and the CPU baselines
+    with g++."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", _SRC, "-o", tmp])
         os.replace(tmp, _LIB_PATH)
+    if force or not os.path.exists(_CPB_PATH) or os.path.getmtime(_CPB_PATH) < os.path.getmtime(_CPB_SRC):
+        tmp = _CPB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O3", "-std=c++17", "-pthread", "-fPIC", "-shared", _CPB_SRC, "-o", tmp])
+        os.replace(tmp, _CPB_PATH)
     return _LIB_PATH
+
+
+def _load_baselines():
+    global _cpb
+    if _cpb is None:
+        build()
+        lib = ctypes.CDLL(_CPB_PATH)
+        i32, u64, vp = ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p
+        lib.cpb_parallel_lsd.restype = i32
+        lib.cpb_parallel_lsd.argtypes = [i32, vp, vp, u64, i32, i32, i32, vp, vp]
+        lib.cpb_std_stable_sort.restype = i32
+        lib.cpb_std_stable_sort.argtypes = [i32, vp, vp, u64, i32, i32, vp, vp]
+        lib.cpb_hardware_threads.restype = i32
+        lib.cpb_hardware_threads.argtypes = []
+        _cpb = lib
+    return _cpb
+
+
+def hardware_threads() -> int:
+    """Host threads the multi-threaded baseline uses by default."""
+    return int(_load_baselines().cpb_hardware_threads())
+
+
+def _baseline_call(fn, key_type, keys, vals, begin_bit, end_bit, *extra):
+    end_bit = key_bits(key_type) if end_bit is None else end_bit
+    k = _keys(key_type, keys)
+    ko = np.empty_like(k)
+    v = None if vals is None else np.ascontiguousarray(vals, dtype=np.uint32)
+    vo = None if v is None else np.empty_like(v)
+    args = [_kt(key_type), _ptr(k), _ptr(v), k.size, begin_bit, end_bit, *extra, _ptr(ko), _ptr(vo)]
+    if fn(*args) != 0:
+        raise ValueError("bad arguments")
+    return ko if v is None else (ko, vo)
+
+
+def parallel_sort(key_type: str, keys, vals=None, begin_bit: int = 0, end_bit: int | None = None,
+                  threads: int | None = None):
+    """The multi-threaded CPU LSD baseline (stable ascending; not the oracle)."""
+    lib = _load_baselines()
+    return _baseline_call(lib.cpb_parallel_lsd, key_type, keys, vals, begin_bit, end_bit,
+                          threads if threads else hardware_threads())
+
+
+def std_stable_sort(key_type: str, keys, vals=None, begin_bit: int = 0, end_bit: int | None = None):
+    """std::stable_sort of the ordered field on one thread (not the oracle)."""
+    return _baseline_call(_load_baselines().cpb_std_stable_sort, key_type, keys, vals, begin_bit, end_bit)
 
 
 def use_library(path: str) -> None:
