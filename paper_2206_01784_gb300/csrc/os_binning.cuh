@@ -10,28 +10,40 @@
 //     The copy covers the 16-byte-aligned span around the tile, so tiles that
 //     start anywhere (segments of a batch) still use it; plain loads are the
 //     fallback when that span would leave the array;
-//  3. homogeneous-tile short-circuit: if every key of the tile has the same
-//     digit, ranking and local reorganisation are skipped and the tile is
-//     written straight to its bin (Section 3, last paragraph of the kernel
-//     description);
-//  4. warp-level multi-split ranking: each warp walks its keys in 32-wide
+//  3. early counts: each warp counts the digits of its part of the tile with
+//     shared-memory atomics (the paper's privatised, atomically updated
+//     histograms of the upfront kernel, here per warp and per tile);
+//  4. thread i publishes (L, count of digit i) in the tile's status counter
+//     and sends the first round of its look-back over the preceding tiles'
+//     counters of digit i (Section 3, decoupled look-back); a block scan of
+//     the counts gives the tile-relative bin starts. Homogeneous-tile
+//     short-circuit: if every key has the same digit, ranking and local
+//     reorganisation are skipped and the tile is written straight to its
+//     bin (Section 3, last paragraph of the kernel description);
+//  5. each warp's per-digit counters start at the local position of its
+//     first key of that digit (tile bin start plus the lower warps' counts);
+//  6. warp-level multi-split ranking: each warp walks its keys in 32-wide
 //     batches and finds the lanes holding the same digit, either as in the
 //     paper with one ballot per digit bit ANDed together, or by having every
 //     lane OR its bit into a per-warp shared-memory mask word of its digit
 //     (OR commutes, so the mask read back is exact whatever the order of the
-//     atomics). The lowest lane of each group bumps the warp's per-digit count
-//     and the group reads the old value (Section 3, WLMS paragraph). A
+//     atomics). The lowest lane of each group bumps the warp's counter of the
+//     digit and the group reads the old value (Section 3, WLMS paragraph):
+//     with counters that start at local positions, that is the key's place
+//     in the tile's shared-memory bins, and the key is written there at once.
+//     Every kRoundEvery batches the look-back's round in flight is folded in
+//     and the next one sent, so its L2 round trips ride along the ranking. A
 //     __match_any_sync per key measured 1.7x slower than the ballots on
 //     GB300 (the match instruction saturates the ADU pipe) and is not used;
-//  5. block-wide scan of the per-warp counts: tile digit counts for the chained
-//     scan and tile-relative bin starts for the local reorganisation;
-//  6. thread i publishes (L, count of digit i) in the tile's status counter,
-//     the keys (then the values) are reorganised into their local bins in
-//     shared memory, then thread i walks the preceding tiles' counters for
-//     digit i (decoupled look-back, several counters per round trip, bounded
-//     wait) and publishes (G, inclusive prefix);
-//  7. runs of keys (and values) are copied from the shared-memory bins to
+//     the values follow the keys' positions;
+//  7. the look-back ends (bounded wait) and publishes (G, inclusive prefix),
+//     and runs of keys (and values) are copied from the shared-memory bins to
 //     their global bins, consecutive threads writing consecutive addresses.
+//
+// The paper's block publishes its counts after ranking; counting first
+// publishes them a ranking earlier, so a tile's predecessors' counts are
+// there by the time its ranking ends, and the separate reorganisation loop
+// (re-reading each key's digit offset) disappears.
 //
 // In segmented mode (os_sort_batch) every segment is a sort of its own: its
 // tiles form one look-back chain that starts at the segment's first tile, and
@@ -149,11 +161,12 @@ __device__ __forceinline__ uint32_t wlms_rank(uint32_t* msk, uint32_t* cnt, uint
   return old + below;
 }
 
-// Decoupled look-back of one digit (step 6b) in rounds: issue() reads the
-// counters of up to W preceding tiles (one L2 round trip), consume() folds in
-// what came back - stopping at a counter not yet published, which the next
-// round reads again - until a G counter or the chain's first tile is reached,
-// and then publishes this tile's (G, inclusive prefix).
+// Decoupled look-back of one digit in rounds: issue() reads the counters of
+// up to W preceding tiles (one L2 round trip), consume() folds in what came
+// back - stopping at a counter not yet published, which the next round reads
+// again - until a G counter or the chain's first tile is reached, and then
+// publishes this tile's (G, inclusive prefix). A round may stay in flight
+// while the block does other work between issue() and consume().
 template <int W>
 struct Lookback {
   uint32_t s[W];       // counters of the round in flight
@@ -191,8 +204,31 @@ struct Lookback {
     }
     if (done) publish_global();
   }
+  // rounds until the walk ends, each waiting for its reads; a wait past the
+  // poll limit records a timeout and still publishes (the successors' walks
+  // then end instead of timing out one after another)
+  __device__ __forceinline__ void finish(const PassArgs& a, uint32_t chain_first, int digit) {
+    uint32_t spins = 0;
+    while (!done) {
+      issue(a.status, chain_first, digit);
+      consume();
+      if (done) break;
+      if (++spins >= a.spin_limit) {
+        atomicOr(a.error, kErrTimeout);
+        break;
+      }
+      if ((spins & 255u) == 0 && (ld_relaxed_gpu(a.error) & kErrTimeout)) break;
+    }
+    if (!done) publish_global();
+  }
 };
 constexpr int kLookbackWindow = 4;
+// Ranking batches between two look-back rounds: about one L2 round trip of
+// ranking work, so a round's reads have come back when it is consumed.
+#ifndef OS_ROUND_EVERY
+#define OS_ROUND_EVERY 8
+#endif
+constexpr int kRoundEvery = OS_ROUND_EVERY;
 
 template <int KBITS, bool PAIRS, int CFG, int RANK, int FLIP, bool FULL>
 __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* smem, const TileCtx& c) {
@@ -202,7 +238,8 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
 
   K* kt = reinterpret_cast<K*>(smem) + c.koff;
   uint32_t* vt = reinterpret_cast<uint32_t*>(smem + C::kbuf_bytes) + c.voff;
-  // [NW][256] lane masks of the current batch, then [NW][256] running counts
+  // [NW][256] lane masks of the current batch, then [NW][256] digit counts
+  // (turned into running local positions before the ranking)
   uint32_t* whist = reinterpret_cast<uint32_t*>(smem + C::kbuf_bytes + C::vbuf_bytes);
   uint32_t* wcnt = whist + NW * kRadix;
   uint32_t* dstart = whist + 2 * NW * kRadix;  // [256] tile-local start of each digit's bin
@@ -224,11 +261,21 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
   const bool publish = (int64_t)tile != a.fault_tile;
   const bool chain_head = tile == c.chain_first;
 
+  // this warp's lane masks and counts start at zero
+  uint32_t* wmsk = whist + warp * kRadix;
+  uint32_t* wc = wcnt + warp * kRadix;
+#pragma unroll
+  for (int i = lane; i < kRadix; i += 32) {
+    wmsk[i] = 0u;
+    wc[i] = 0u;
+  }
+
   if (c.bulk) {
     if (!mbar_wait_bounded(&mbar[0], 0, kBulkWaitLimit)) atomicOr(a.error, kErrTimeout);
   } else {
     __syncthreads();
   }
+  __syncwarp();
 
   // keys of this thread: warp-striped, batch i of warp w covers tile positions
   // [w*IPT*32 + i*32, +32), so batch order and lane order are input order
@@ -240,54 +287,41 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
     key[i] = load_transform<FLIP>((FULL || idx < count) ? kt[idx] : K(0));
   }
 
-  // 3. homogeneous-tile check: any digit bit differing from the first key's
-  const K first = load_transform<FLIP>(kt[0]);
-  const K digit_bits = (K)mask << shift;
-  K differ = 0;
+  // 3. early counts: each warp's digit histogram of its part of the tile
 #pragma unroll
-  for (int i = 0; i < IPT; ++i) {
-    const bool valid = FULL || wbase + i * 32 < count;
-    if (valid) differ |= (key[i] ^ first) & digit_bits;
-  }
-  const bool homogeneous = __syncthreads_or(differ != 0) == 0;
-  const uint32_t d0 = digit_of(first, shift, mask, dxor);
+  for (int i = 0; i < IPT; ++i)
+    if (FULL || wbase + i * 32 < count) atomicAdd(wc + digit_of(key[i], shift, mask, dxor), 1u);
+  const uint32_t d0 = digit_of(load_transform<FLIP>(kt[0]), shift, mask, dxor);
+  __syncthreads();
 
+  // 4. tile digit counts: publish L now, and start the look-back (step 6),
+  //    whose rounds then ride along the ranking; a tile whose keys share one
+  //    digit skips ranking and reorganisation (homogeneous-tile short-circuit)
   uint32_t digit_count = 0;  // thread d < 256: keys of digit d in this tile
+  if (tid < kRadix) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) digit_count += wcnt[w * kRadix + tid];
+    if (publish)
+      st_relaxed_gpu(status + tid, ((chain_head ? kFlagGlobal : kFlagLocal) << kStatusShift) | digit_count);
+  }
+  const bool walker = tid < kRadix && !chain_head;
+  Lookback<kLookbackWindow> lb;
+  bool issued = false;
+  if (walker) {
+    lb.start(tile, c.chain_first);
+    lb.mine = publish ? status + tid : nullptr;
+    lb.own = digit_count;
+    lb.issue(a.status, c.chain_first, tid);
+    issued = true;
+  }
+  const bool homogeneous = __syncthreads_or(tid < kRadix && digit_count == count) != 0;
 
   if (homogeneous) {
     if (PAIRS && c.bulk && !mbar_wait_bounded(&mbar[1], 0, kBulkWaitLimit)) atomicOr(a.error, kErrTimeout);
-    if (tid < kRadix) {
-      digit_count = (uint32_t)tid == d0 ? count : 0u;
-      dstart[tid] = 0u;
-      if (publish)
-        st_relaxed_gpu(status + tid, ((chain_head ? kFlagGlobal : kFlagLocal) << kStatusShift) | digit_count);
-    }
+    if (tid < kRadix) dstart[tid] = 0u;
   } else {
-    // 4. warp-level multi-split ranking; rank = keys of the same digit before
-    //    this one in the warp's part of the tile
-    uint32_t* wmsk = whist + warp * kRadix;
-    uint32_t* wc = wcnt + warp * kRadix;
-    uint32_t rank2[IPT / 2 + 1];  // two 16-bit ranks per register (ranks < T <= 2^16)
-    const uint32_t lane_bit = 1u << lane;
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-      const bool valid = FULL || wbase + i * 32 < count;
-      const bool smask = RANK == kRankHybrid && (i & 1);
-      const uint32_t r = wlms_rank<FULL>(wmsk, wc, digit_of(key[i], shift, mask, dxor), valid, lane_bit, smask);
-      if (i & 1)
-        rank2[i / 2] |= r << 16;
-      else
-        rank2[i / 2] = r;
-    }
-    __syncthreads();
-
-    // 5. tile digit counts, publish L, per-warp exclusive offsets
-    if (tid < kRadix) {
-#pragma unroll
-      for (int w = 0; w < NW; ++w) digit_count += wcnt[w * kRadix + tid];
-      if (publish)
-        st_relaxed_gpu(status + tid, ((chain_head ? kFlagGlobal : kFlagLocal) << kStatusShift) | digit_count);
-    }
+    // 5. block scan of the counts: tile-local bin starts, and each warp's
+    //    counters set to where its first key of each digit goes
     const uint32_t excl = block_exclusive_sum<NT>(tid < kRadix ? digit_count : 0u, misc);
     if (tid < kRadix) {
       uint32_t run = excl;
@@ -301,20 +335,29 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
     }
     __syncthreads();
 
-    // 6a. local reorganisation of the keys into shared-memory bins; for pairs
-    //     the positions are kept (two 16-bit positions per register)
+    // 6a. warp-level multi-split ranking straight to local positions: each
+    //     key is written into its shared-memory bin as soon as it is ranked
+    //     (every key is in registers since the barrier above); for pairs the
+    //     positions are kept, two 16-bit positions per register
     uint32_t pos2[PAIRS ? IPT / 2 + 1 : 1];
+    const uint32_t lane_bit = 1u << lane;
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       const bool valid = FULL || wbase + i * 32 < count;
-      const uint32_t r = (i & 1) ? (rank2[i / 2] >> 16) : (rank2[i / 2] & 0xFFFFu);
-      const uint32_t p = valid ? wc[digit_of(key[i], shift, mask, dxor)] + r : 0u;
+      const bool smask = RANK == kRankHybrid && (i & 1);
+      const uint32_t p = wlms_rank<FULL>(wmsk, wc, digit_of(key[i], shift, mask, dxor), valid, lane_bit, smask);
       if (valid) kt[p] = key[i];
       if (PAIRS) {
         if (i & 1)
           pos2[i / 2] |= p << 16;
         else
           pos2[i / 2] = p;
+      }
+      // a look-back round: fold in the last one's reads, send the next
+      if (i % kRoundEvery == kRoundEvery - 1 && i + 1 < IPT && walker) {
+        if (issued) lb.consume();
+        issued = !lb.done;
+        if (issued) lb.issue(a.status, c.chain_first, tid);
       }
     }
     if (PAIRS) {
@@ -333,30 +376,13 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
     }
   }
 
-  // 6b. decoupled look-back: thread d walks back over the counters of digit
-  //     d in the preceding tiles of the chain, up to kLookbackWindow per round
-  //     trip, until it reaches a G counter; then it publishes (G, inclusive
-  //     prefix) for this tile
+  // 6b. the rest of the decoupled look-back: thread d walks back over the
+  //     counters of digit d in the preceding tiles of the chain until it
+  //     reaches a G counter; then it publishes (G, inclusive prefix)
   uint32_t exclusive = 0;
-  if (tid < kRadix && !chain_head) {
-    Lookback<kLookbackWindow> lb;
-    lb.start(tile, c.chain_first);
-    lb.mine = publish ? status + tid : nullptr;
-    lb.own = digit_count;
-    uint32_t spins = 0;
-    while (!lb.done) {
-      lb.issue(a.status, c.chain_first, tid);
-      lb.consume();  // publishes G when the walk ends
-      if (lb.done) break;
-      if (++spins >= a.spin_limit) {
-        atomicOr(a.error, kErrTimeout);
-        break;
-      }
-      if ((spins & 255u) == 0 && (ld_relaxed_gpu(a.error) & kErrTimeout)) break;
-    }
-    // a wait that gave up still publishes (the error is recorded; the
-    // successors' walks then end instead of timing out one after another)
-    if (!lb.done) lb.publish_global();
+  if (walker) {
+    if (issued) lb.consume();
+    lb.finish(a, c.chain_first, tid);
     exclusive = lb.exclusive;
   }
   if (tid < kRadix) {
@@ -477,9 +503,6 @@ __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS, CFG>::NT, BinningC
   __syncthreads();
   const TileCtx c = s_ctx;
   if (c.count == 0) return;  // no tile left (or the workspace's counters were not reset)
-  // per-warp counters start at zero; the block barrier of the homogeneity
-  // test orders this before their first use
-  for (int i = tid; i < 2 * NW * kRadix; i += NT) whist[i] = 0;
 
   // 2. plain staging when the bulk copy does not apply
   if (!c.bulk) {
