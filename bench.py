@@ -242,11 +242,12 @@ def time_cpu_baselines(keys_np, vals_np, key_type: str, full_std: bool = True):
 
 
 def measure_config(torch, osw, workload, np, dev, key_type: str, log2n: int, pairs: bool, dist: str, seed: int,
-                   steps: int = 10, warmup: int = 3):
-    """One more workload configuration through os_sort_pairs / os_sort_keys,
-    timed like the headline (CUDA events around the steps, launch times from
-    the library's profile hooks): GKeys/s, ms per step, the binning kernel's
-    and the whole step's fraction of the HBM roofline."""
+                   steps: int = 10, warmup: int = 3, radix_bits: int = 8):
+    """One more workload configuration through os_sort_pairs_ex /
+    os_sort_keys_ex, timed like the headline (CUDA events around the steps,
+    launch times from the library's profile hooks): GKeys/s, ms per step, the
+    binning kernel's and the whole step's fraction of the HBM roofline.
+    radix_bits: bits per digit place."""
     n = 1 << log2n
     bits = KEY_BITS[key_type]
     kbytes = bits // 8
@@ -260,19 +261,22 @@ def measure_config(torch, osw, workload, np, dev, key_type: str, log2n: int, pai
     ws = torch.empty(lay.total_bytes, dtype=torch.uint8, device=dev)
     sp = torch.cuda.current_stream(dev).cuda_stream
 
+    places = (bits + radix_bits - 1) // radix_bits
+
     def step():
         if pairs:
-            rc = osw.os_sort_pairs(kt, keys.data_ptr(), ko.data_ptr(), vals.data_ptr(), vo.data_ptr(), n, 0, bits,
-                                   ws.data_ptr(), ws.numel(), sp)
+            rc = osw.os_sort_pairs_ex(kt, keys.data_ptr(), ko.data_ptr(), vals.data_ptr(), vo.data_ptr(), n, 0, bits,
+                                      ws.data_ptr(), ws.numel(), sp, radix_bits=radix_bits)
         else:
-            rc = osw.os_sort_keys(kt, keys.data_ptr(), ko.data_ptr(), n, 0, bits, ws.data_ptr(), ws.numel(), sp)
+            rc = osw.os_sort_keys_ex(kt, keys.data_ptr(), ko.data_ptr(), n, 0, bits, ws.data_ptr(), ws.numel(), sp,
+                                     radix_bits=radix_bits)
         if rc != osw.OS_OK:
             raise osw.OnesweepError(rc, "sort")
 
     for _ in range(warmup):
         step()
     torch.cuda.synchronize(dev)
-    cap = steps * (lay.num_places + 1) + 16
+    cap = steps * (places + 1) + 16
     osw.os_profile_start(cap)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -289,12 +293,34 @@ def measure_config(torch, osw, workload, np, dev, key_type: str, log2n: int, pai
         raise RuntimeError("configuration output not sorted")
     peak, _ = hbm_peak()
     bin_ms = statistics.mean([m for k, _, m in recs if k == 1])
+    hist_ms = statistics.mean([m for k, _, m in recs if k == 0])
     per_pass = n * 2 * (kbytes + (4 if pairs else 0))
-    step_bytes = n * kbytes + lay.num_places * per_pass
-    return {"workload": workload_name(n, dist, seed, pairs, key_type), "keys": n, "places": lay.num_places,
-            "gkeys_per_s": n / ms / 1e6, "ms_per_step": ms, "binning_avg_ms": bin_ms,
-            "binning_frac": per_pass / (bin_ms / 1e3) / 1e9 / peak,
+    step_bytes = n * kbytes + places * per_pass
+    return {"workload": workload_name(n, dist, seed, pairs, key_type), "keys": n, "places": places,
+            "radix_bits": radix_bits, "gkeys_per_s": n / ms / 1e6, "ms_per_step": ms, "binning_avg_ms": bin_ms,
+            "histogram_avg_ms": hist_ms, "binning_frac": per_pass / (bin_ms / 1e3) / 1e9 / peak,
             "step_frac": step_bytes / (ms / 1e3) / 1e9 / peak, "steps": steps}
+
+
+# Section 4, Table 2 (A100, 256M random u32 keys only): digit width d ->
+# (histogram us, partition us per pass); context for the GB300 sweep.
+PAPER_TABLE2_A100 = {5: (652, 1573), 6: (653, 1685), 7: (679, 1812), 8: (747, 1995), 9: (655, 2541)}
+
+
+def measure_digit_widths(torch, osw, workload, np, dev, log2n: int = 28, steps: int = 5):
+    """Table 2's sweep on this GPU: 2^log2n uniform u32 keys only, sorted with
+    d = 5..8 bits per digit place; per d the histogram and per-pass binning
+    times (us), the per-bit cost of a pass and the whole sort."""
+    rows = {}
+    for d in (5, 6, 7, 8):
+        r = measure_config(torch, osw, workload, np, dev, "u32", log2n, False, "uniform", 1, steps=steps, radix_bits=d)
+        rows[str(d)] = {"passes": r["places"], "histogram_us": r["histogram_avg_ms"] * 1e3,
+                        "partition_us": r["binning_avg_ms"] * 1e3, "partition_per_bit_us": r["binning_avg_ms"] * 1e3 / d,
+                        "sort_ms": r["ms_per_step"], "gkeys_per_s": r["gkeys_per_s"], "binning_frac": r["binning_frac"]}
+        torch.cuda.empty_cache()
+    return {"workload": workload_name(1 << log2n, "uniform", 1, False, "u32"), "rows": rows,
+            "paper_a100_us": {str(d): {"histogram_us": h, "partition_us": p, "partition_per_bit_us": round(p / d)}
+                              for d, (h, p) in PAPER_TABLE2_A100.items()}}
 
 
 def measure_copy_ceiling(torch, dev, nbytes: int):
@@ -656,7 +682,7 @@ def main():
         if not ok:
             raise RuntimeError("end-to-end result differs from the device result")
 
-    batched = serving = configs = copy_ceiling = None
+    batched = serving = configs = copy_ceiling = digit_widths = None
     if world == 1 and not args.no_extras:
         # the other workload configurations at full size (extras, not the headline)
         configs = {}
@@ -665,6 +691,7 @@ def main():
                                                         ("f32_pairs_256m", "f32", 28, True, "normal", 9)):
             configs[name] = measure_config(torch, osw, workload, np, dev, kt_, log2n_, pairs_, dist_, seed_)
             torch.cuda.empty_cache()
+        digit_widths = measure_digit_widths(torch, osw, workload, np, dev)
         copy_ceiling = measure_copy_ceiling(torch, dev, n * (kbytes + (4 if pairs else 0)))
         if e2e is not None:
             moved = e2e["h2d_bytes_per_step"] + e2e["d2h_bytes_per_step"]
@@ -696,7 +723,8 @@ def main():
                              "larger than L2"},
             "roofline": roofline, "roofline_step": step_roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "gpu": torch.cuda.get_device_name(dev),
-            "batched": batched, "serving": serving, "configs": configs, "copy_ceiling": copy_ceiling,
+            "batched": batched, "serving": serving, "configs": configs, "digit_widths": digit_widths,
+            "copy_ceiling": copy_ceiling,
             "paper_context": "A100-80GB: 29.4 GKey/s, 256M u32 keys only (different hardware and workload)",
         }
         print(json.dumps(line), flush=True)

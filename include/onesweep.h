@@ -277,6 +277,18 @@ OS_API int os_set_tile_config_bucket(int key_bits, int value_bytes, int bucket, 
 OS_API int os_get_tile_config_bucket(int key_bits, int value_bytes, int bucket);
 
 /*
+ * The process-wide digit width d (bits per digit place; Section 3, and the
+ * d sweep of Section 4, Table 2) per size bucket, used by single-array sorts
+ * whose per-call options leave radix_bits at 0 (no options, or
+ * os_sort_options.radix_bits == 0); 8 until set. A sort that names a tile
+ * variant other than 4 and leaves radix_bits at 0 uses 8; batches always use
+ * 8. radix_bits: 5-8, else OS_ERR_INVALID_ARG. The get call returns the
+ * width, or -1 for invalid arguments. The sorted output never depends on d.
+ */
+OS_API int os_set_radix_bits_bucket(int key_bits, int value_bytes, int bucket, int radix_bits);
+OS_API int os_get_radix_bits_bucket(int key_bits, int value_bytes, int bucket);
+
+/*
  * Launch timing for benchmarks (not part of the method). os_profile_start
  * makes every later kernel launch of the library record a CUDA event pair on
  * its own stream, for up to `capacity` launches. os_profile_stop waits for
@@ -304,13 +316,22 @@ OS_API int os_profile_stop(os_launch_time *out, int max, int *count);
  * their own. opt == NULL or opt->tile_config == -1 means the process-wide
  * choice for the sort's size bucket; any other value must be below
  * os_num_tile_configs() (else OS_ERR_INVALID_ARG). Results are identical for
- * every variant. `reserved` must be 0. The library holds no other per-call
- * state: calls on different streams with different workspaces may run
- * concurrently from any number of host threads.
+ * every variant. The library holds no other per-call state: calls on
+ * different streams with different workspaces may run concurrently from any
+ * number of host threads.
+ *
+ * radix_bits: bits per digit place d (Section 3; Section 4, Table 2 measures
+ * d = 5..9). 0 means the process-wide choice (os_set_radix_bits_bucket; 8,
+ * with 256 bins and p = ceil(bits / 8) passes, until set); 5, 6 or 7 sort
+ * with 2^d bins in ceil(bits / d) passes, using tile variant
+ * 4 (tile_config must then be -1 or 4) and single arrays only
+ * (os_sort_batch_ex rejects them). Any other value: OS_ERR_INVALID_ARG. The
+ * sorted output is the same for every d; only the number and cost of the
+ * passes change. Workspace sizes do not depend on d.
  */
 typedef struct {
     int tile_config;
-    uint32_t reserved;
+    uint32_t radix_bits;
 } os_sort_options;
 
 OS_API int os_sort_keys_ex(int key_type, const void *keys_in, void *keys_out, uint64_t n, int begin_bit,

@@ -1,17 +1,18 @@
-"""Autotuner for the binning kernel's variants.
+"""Autotuner for the binning kernel's variants and digit width.
 
 The library carries os_num_tile_configs() variants of the digit-binning kernel
 (tile geometry - threads per block and keys per thread - times the digit
-ranking method) and keeps one active variant per (key width, payload, size
-bucket). ``tune`` times every variant on seeded uniform keys of a size
-representative of each bucket (CUDA events around whole sorts), installs the
-fastest through os_set_tile_config_bucket and returns the table; ``save`` /
-``load`` / ``apply`` keep tables across processes. Results of a sort never
-depend on the variant - only its speed does - and workspaces are sized for the
-smallest tile, so a table can be applied at any time between calls.
-
-The radix width stays 8 bits: the paper's Table 2 finds 8-bit digit places
-the most efficient per bit, and 8 bits is what the kernels are built for.
+ranking method) and digit widths d of 5 to 8 bits (Section 4, Table 2: fewer
+bits make each pass cheaper and the sort longer), and keeps one active
+(variant, d) per (key width, payload, size bucket). ``tune`` times every
+variant at d = 8 and variant 4 (the one narrower digits run) at each smaller
+d on seeded uniform keys of a size representative of each bucket (CUDA events
+around whole sorts), installs the fastest through os_set_tile_config_bucket
+and os_set_radix_bits_bucket and returns the table; ``save`` / ``load`` /
+``apply`` keep tables across processes. Results of a sort never depend on the
+variant or on d - only its speed does - and workspaces are sized for the
+smallest tile and the most places, so a table can be applied at any time
+between calls.
 """
 from __future__ import annotations
 
@@ -25,16 +26,21 @@ from . import workload
 BUCKET_SIZES = {0: 1 << 15, 1: 1 << 19, 2: 1 << 23, 3: 1 << 26}
 
 
-def _time_sort(kt, k, v, ko, vo, n, kb, ws, steps, warmup, torch):
+NARROW_VARIANT = 4          # the tile variant of digits narrower than 8 bits
+RADIX_BITS = (5, 6, 7, 8)  # digit widths the library carries
+
+
+def _time_sort(kt, k, v, ko, vo, n, kb, ws, steps, warmup, torch, cfg=None, radix_bits=None):
     s = torch.cuda.current_stream()
     sp = s.cuda_stream
 
     def one():
         if v is None:
-            rc = osw.os_sort_keys(kt, k.data_ptr(), ko.data_ptr(), n, 0, kb, ws.data_ptr(), ws.numel(), sp)
+            rc = osw.os_sort_keys_ex(kt, k.data_ptr(), ko.data_ptr(), n, 0, kb, ws.data_ptr(), ws.numel(), sp,
+                                     tile_config=cfg, radix_bits=radix_bits)
         else:
-            rc = osw.os_sort_pairs(kt, k.data_ptr(), ko.data_ptr(), v.data_ptr(), vo.data_ptr(), n, 0, kb,
-                                   ws.data_ptr(), ws.numel(), sp)
+            rc = osw.os_sort_pairs_ex(kt, k.data_ptr(), ko.data_ptr(), v.data_ptr(), vo.data_ptr(), n, 0, kb,
+                                      ws.data_ptr(), ws.numel(), sp, tile_config=cfg, radix_bits=radix_bits)
         if rc != osw.OS_OK:
             raise osw.OnesweepError(rc, "autotune sort")
 
@@ -50,11 +56,19 @@ def _time_sort(kt, k, v, ko, vo, n, kb, ws, steps, warmup, torch):
     return e0.elapsed_time(e1) / steps
 
 
-def tune(key_bits=(32, 64), value_bytes=(0, 4), buckets=None, steps: int = 5, warmup: int = 2, seed: int = 1234,
-         sizes: dict | None = None, verbose: bool = False) -> dict:
-    """Times every variant and installs the fastest per (key bits, value bytes, bucket).
+def candidates(radix_bits=RADIX_BITS):
+    """(tile variant, digit width) pairs the tuner times: every variant with
+    8-bit digits, and the narrow-digit variant at each smaller width."""
+    out = [(cfg, 8) for cfg in range(osw.os_num_tile_configs())] if 8 in radix_bits else []
+    return out + [(NARROW_VARIANT, d) for d in sorted(radix_bits) if d != 8]
 
-    Returns {(key_bits, value_bytes, bucket): {"cfg": best, "ms": [per variant]}}."""
+
+def tune(key_bits=(32, 64), value_bytes=(0, 4), buckets=None, steps: int = 5, warmup: int = 2, seed: int = 1234,
+         sizes: dict | None = None, verbose: bool = False, radix_bits=RADIX_BITS) -> dict:
+    """Times every candidate and installs the fastest per (key bits, value bytes, bucket).
+
+    Returns {(key_bits, value_bytes, bucket): {"cfg": variant, "radix_bits": d,
+    "ms": {"cfg/d": ms}, "n": keys}}."""
     import numpy as np
     import torch
 
@@ -75,16 +89,17 @@ def tune(key_bits=(32, 64), value_bytes=(0, 4), buckets=None, steps: int = 5, wa
                     v = torch.from_numpy(workload.iota_u32(n).view(np.int32)).to(dev)
                     vo = torch.empty_like(v)
                 ws = osw.workspace(kt, n, vb, 0, kb, dev)
-                times = []
-                for cfg in range(osw.os_num_tile_configs()):
-                    osw.os_set_tile_config_bucket(kb, vb, b, cfg)
-                    times.append(_time_sort(kt, k, v, ko, vo, n, kb, ws, steps, warmup, torch))
-                best = min(range(len(times)), key=times.__getitem__)
-                osw.os_set_tile_config_bucket(kb, vb, b, best)
-                table[(kb, vb, b)] = {"cfg": best, "ms": times, "n": n}
+                times = {}
+                for cfg, d in candidates(radix_bits):
+                    times[(cfg, d)] = _time_sort(kt, k, v, ko, vo, n, kb, ws, steps, warmup, torch, cfg, d)
+                best = min(times, key=times.__getitem__)
+                osw.os_set_tile_config_bucket(kb, vb, b, best[0])
+                osw.os_set_radix_bits_bucket(kb, vb, b, best[1])
+                table[(kb, vb, b)] = {"cfg": best[0], "radix_bits": best[1],
+                                      "ms": {f"{c}/{d}": t for (c, d), t in times.items()}, "n": n}
                 if verbose:
-                    print(f"key_bits={kb} value_bytes={vb} bucket={b} n={n}: variant {best} "
-                          f"({times[best]:.3f} ms; all {[round(t, 3) for t in times]})", flush=True)
+                    print(f"key_bits={kb} value_bytes={vb} bucket={b} n={n}: variant {best[0]}, {best[1]}-bit "
+                          f"digits ({times[best]:.3f} ms)", flush=True)
                 del k, ko, v, vo, ws
     return table
 
@@ -95,11 +110,15 @@ def apply(table: dict) -> None:
         rc = osw.os_set_tile_config_bucket(kb, vb, b, int(rec["cfg"]))
         if rc != osw.OS_OK:
             raise osw.OnesweepError(rc, "os_set_tile_config_bucket")
+        rc = osw.os_set_radix_bits_bucket(kb, vb, b, int(rec.get("radix_bits", 8)))
+        if rc != osw.OS_OK:
+            raise osw.OnesweepError(rc, "os_set_radix_bits_bucket")
 
 
 def current() -> dict:
     """The active variant of every (key bits, value bytes, bucket)."""
-    return {(kb, vb, b): {"cfg": osw.os_get_tile_config_bucket(kb, vb, b)}
+    return {(kb, vb, b): {"cfg": osw.os_get_tile_config_bucket(kb, vb, b),
+                          "radix_bits": osw.os_get_radix_bits_bucket(kb, vb, b)}
             for kb in (32, 64) for vb in (0, 4) for b in range(osw.os_num_size_buckets())}
 
 

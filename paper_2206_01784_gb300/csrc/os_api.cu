@@ -49,6 +49,22 @@ const BinningLaunch kBinningLaunch[2][2][2][4] = {
      {OS_BINNING_ROW(64, keys, seg), OS_BINNING_ROW(64, pairs, seg)}}};
 #undef OS_BINNING_ROW
 
+// Digits narrower than 8 bits (os_sort_options.radix_bits 5-7)
+#define OS_DECLARE_RB(RB)                                                                 \
+  cudaError_t launch_binning_rb##RB##_32(bool, int, const PassArgs&, cudaStream_t);       \
+  cudaError_t launch_binning_rb##RB##_64(bool, int, const PassArgs&, cudaStream_t);
+OS_DECLARE_RB(5)
+OS_DECLARE_RB(6)
+OS_DECLARE_RB(7)
+#undef OS_DECLARE_RB
+using BinningLaunchRb = cudaError_t (*)(bool, int, const PassArgs&, cudaStream_t);
+constexpr int kMinRadixBits = 5;
+// [64-bit][radix bits - kMinRadixBits]
+const BinningLaunchRb kBinningLaunchRb[2][3] = {
+    {launch_binning_rb5_32, launch_binning_rb6_32, launch_binning_rb7_32},
+    {launch_binning_rb5_64, launch_binning_rb6_64, launch_binning_rb7_64}};
+constexpr int kMaxPlaces = 16;  // 64-bit keys in 5-bit digits: 13 places
+
 // Binning kernel variants: tile geometry (4) x digit-ranking method (3);
 // variant v uses geometry v % 4 and ranking v / 4 (0: one ballot per digit
 // bit; 1: adaptive - ballots where the place is skewed, else the hybrid;
@@ -72,6 +88,14 @@ int g_tile_cfg[2][2][kSizeBuckets] = {{OS_FOUR_DEFAULTS, OS_FOUR_DEFAULTS}, {OS_
 #undef OS_FOUR_DEFAULTS
 
 int size_bucket(uint64_t n) { return n < (1u << 16) ? 0 : n < (1u << 20) ? 1 : n < (1u << 24) ? 2 : 3; }
+
+// Process-wide digit width per (key width, payload, size bucket), for sorts
+// whose options leave radix_bits at 0 (the autotuner sets it).
+std::atomic<int> g_radix_bits[2][2][kSizeBuckets];
+int get_radix_bits(int key_bits, bool pairs, int bucket) {
+  const int v = g_radix_bits[key_bits == 64][pairs][bucket].load(std::memory_order_relaxed);
+  return v == 0 ? kRadixBits : v;
+}
 
 int get_tile_cfg(int key_bits, bool pairs, int bucket) {
   return __atomic_load_n(&g_tile_cfg[key_bits == 64][pairs][bucket], __ATOMIC_RELAXED);
@@ -99,9 +123,13 @@ uint32_t min_tile_keys(int key_bits, bool pairs) {
   return t;
 }
 
-cudaError_t launch_binning(int key_bits, bool pairs, int cfg, const PassArgs& a, cudaStream_t s) {
+cudaError_t launch_binning(int key_bits, bool pairs, int cfg, const PassArgs& a, cudaStream_t s, int radix_bits) {
   const int flip = (a.flip_in ? 1 : 0) | (a.flip_out ? 2 : 0);
   const int seg = a.seg_offsets != nullptr;
+  if (radix_bits != kRadixBits) {
+    if (seg || radix_bits < kMinRadixBits || radix_bits > kRadixBits) return cudaErrorInvalidValue;
+    return kBinningLaunchRb[key_bits == 64][radix_bits - kMinRadixBits](pairs, flip, a, s);
+  }
   return kBinningLaunch[seg][key_bits == 64][pairs][flip](cfg % kGeometries, cfg / kGeometries, a, s);
 }
 
@@ -124,7 +152,7 @@ constexpr uint32_t kDefaultSpinLimit = 1u << 22;
 constexpr size_t kHeaderBytes = 256;
 constexpr size_t kDoneWord = 1;
 constexpr size_t kTileCounterWord = 16;
-constexpr size_t kSkewWord = 32;  // 8 skewed-place flags of a single sort
+constexpr size_t kSkewWord = 32;  // 16 skewed-place flags of a single sort
 
 // Test hooks (onesweep_debug.h), read once per sort when it is planned.
 std::atomic<int64_t> g_fault_tile{-1};
@@ -188,12 +216,12 @@ bool is_float(int key_type) { return (key_type & 0xFF) == OS_KEY_F32 || (key_typ
 // order). Only the most significant place holds the sign bit, so instead of
 // transforming keys, that place's digit gets its high bit inverted - when the
 // sorted range reaches the sign bit.
-uint32_t signed_top_xor(int key_type, int begin_bit, int end_bit) {
+uint32_t signed_top_xor(int key_type, int begin_bit, int end_bit, int radix_bits = kRadixBits) {
   const int kb = key_bits_of(key_type);
   const int base = key_type & 0xFF;
   if ((base != OS_KEY_I32 && base != OS_KEY_I64) || end_bit != kb || end_bit <= begin_bit) return 0u;
-  const int places = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
-  const int top_width = end_bit - (begin_bit + kRadixBits * (places - 1));
+  const int places = (end_bit - begin_bit + radix_bits - 1) / radix_bits;
+  const int top_width = end_bit - (begin_bit + radix_bits * (places - 1));
   return 1u << (top_width - 1);
 }
 
@@ -202,6 +230,7 @@ struct Plan {
   bool pairs = false;
   int bucket = 0;
   int cfg = 0;               // binning variant (geometry + ranking)
+  int radix_bits = kRadixBits;  // d: bits per digit place
   int places = 0;
   int64_t fault_tile = -1;   // test hooks, read once
   uint32_t spin_limit = 0;
@@ -215,8 +244,11 @@ struct Plan {
 };
 
 // cfg_override: the caller's binning variant, or -1 for the process-wide one.
+// radix_bits: bits per digit place (5-8; narrower digits use tile variant 4,
+// geometry 0 with adaptive ranking), or 0 for the process-wide one (8 when
+// the caller names another variant).
 int make_plan(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_bit, Plan* plan,
-              int cfg_override = -1) {
+              int cfg_override = -1, int radix_bits = 0) {
   const int kb = key_bits_of(key_type);
   if (kb == 0) return OS_ERR_INVALID_ARG;
   if (value_bytes != 0 && value_bytes != 4) return OS_ERR_INVALID_ARG;
@@ -224,11 +256,21 @@ int make_plan(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_
   if (n >= kMaxKeys) return OS_ERR_TOO_LARGE;
   plan->key_bits = kb;
   plan->pairs = value_bytes == 4;
-  plan->places = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
+  if (radix_bits == 0) {
+    radix_bits = get_radix_bits(kb, plan->pairs, size_bucket(n));
+    if (cfg_override >= 0 && cfg_override != kGeometries) radix_bits = kRadixBits;
+  }
+  if (radix_bits < kMinRadixBits || radix_bits > kRadixBits) return OS_ERR_INVALID_ARG;
+  plan->radix_bits = radix_bits;
+  plan->places = (end_bit - begin_bit + radix_bits - 1) / radix_bits;
   plan->bucket = size_bucket(n);
   // the variant is read once: every launch of this sort uses the same one
   if (cfg_override >= kTileConfigs) return OS_ERR_INVALID_ARG;
   plan->cfg = cfg_override >= 0 ? cfg_override : binning_config(kb, plan->pairs, plan->bucket);
+  if (radix_bits != kRadixBits) {
+    if (cfg_override >= 0 && cfg_override != kGeometries) return OS_ERR_INVALID_ARG;
+    plan->cfg = kGeometries;  // geometry 0, adaptive ranking
+  }
   plan->fault_tile = g_fault_tile.load(std::memory_order_relaxed);
   plan->spin_limit = g_spin_limit.load(std::memory_order_relaxed);
   plan->tile = tile_keys_for(kb, plan->pairs, plan->cfg);
@@ -246,7 +288,7 @@ int make_plan(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_
   const uint32_t min_tile = min_tile_keys(kb, plan->pairs);
   const uint64_t launch_keys = n < kStripKeys ? n : kStripKeys;
   const uint64_t max_tiles = (launch_keys + min_tile - 1) / min_tile;
-  // one tile counter per launch: 8 places x strips, for any strip length the
+  // one tile counter per launch: kMaxPlaces places x strips, for any strip length the
   // test hook allows (>= kMinStripKeys rounded down to a tile of < 2^15 keys,
   // then balanced: longer than n / (n / 2^15 + 1) keys; a workspace sized
   // once always fits)
@@ -255,11 +297,11 @@ int make_plan(int key_type, uint64_t n, int value_bytes, int begin_bit, int end_
   std::memset(&L, 0, sizeof(L));
   size_t off = kHeaderBytes;
   L.histogram_offset = off;
-  off = round_up(off + (size_t)8 * kRadix * 4);
+  off = round_up(off + (size_t)kMaxPlaces * kRadix * 4);
   plan->counters = off;
-  off = round_up(off + (size_t)8 * max_strips * 4);
+  off = round_up(off + (size_t)kMaxPlaces * max_strips * 4);
   L.bin_offset_offset = off;
-  off = round_up(off + (size_t)8 * kRadix * 4);
+  off = round_up(off + (size_t)kMaxPlaces * kRadix * 4);
   plan->carry = off;
   off = round_up(off + (size_t)2 * kRadix * 4);
   const size_t slab = (size_t)max_tiles * kRadix * 4;
@@ -320,6 +362,7 @@ int run_histogram(const Plan& plan, int key_type, const void* keys, uint64_t n, 
   h.n = n;
   h.flip = is_float(key_type);
   h.num_places = plan.places;
+  h.radix_bits = plan.radix_bits;
   h.begin_bit = begin_bit;
   h.end_bit = end_bit;
   h.hist = reinterpret_cast<uint32_t*>(ws + plan.layout.histogram_offset);
@@ -330,7 +373,7 @@ int run_histogram(const Plan& plan, int key_type, const void* keys, uint64_t n, 
   const uint64_t first_tiles = (plan.strip < n ? plan.strip : n + plan.tile - 1) / plan.tile;
   h.clear_words = clear_slab0 ? first_tiles * kRadix : 0;
   h.skew = reinterpret_cast<uint32_t*>(ws) + kSkewWord;
-  h.top_xor = signed_top_xor(key_type, begin_bit, end_bit);
+  h.top_xor = signed_top_xor(key_type, begin_bit, end_bit, plan.radix_bits);
   h.descending = is_descending(key_type) ? 1u : 0u;
   const int sms = device_sm_count();
   if (sms <= 0) return OS_ERR_CUDA;
@@ -341,11 +384,12 @@ int run_histogram(const Plan& plan, int key_type, const void* keys, uint64_t n, 
 }
 
 int run_sort(int key_type, const void* keys_in, void* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
-             uint64_t n, int begin_bit, int end_bit, void* ws, size_t ws_bytes, void* stream, int cfg_override = -1) {
+             uint64_t n, int begin_bit, int end_bit, void* ws, size_t ws_bytes, void* stream, int cfg_override = -1,
+             int radix_bits = 0) {
   const bool pairs = vals_in != nullptr || vals_out != nullptr;
   if (pairs && (vals_in == nullptr || vals_out == nullptr)) return OS_ERR_INVALID_ARG;
   Plan plan;
-  int rc = make_plan(key_type, n, pairs ? 4 : 0, begin_bit, end_bit, &plan, cfg_override);
+  int rc = make_plan(key_type, n, pairs ? 4 : 0, begin_bit, end_bit, &plan, cfg_override, radix_bits);
   if (rc != OS_OK) return rc;
   if (n == 0) return OS_OK;
   const size_t kbytes = (size_t)n * (plan.key_bits / 8);
@@ -426,8 +470,8 @@ int run_sort(int key_type, const void* keys_in, void* keys_out, const uint32_t* 
       a.n = strip_len(st);
       a.out_total = (uint32_t)n;
       a.num_tiles = strip_tiles(st);
-      a.shift = begin_bit + kRadixBits * pass;
-      const int width = end_bit - a.shift < kRadixBits ? end_bit - a.shift : kRadixBits;
+      a.shift = begin_bit + plan.radix_bits * pass;
+      const int width = end_bit - a.shift < plan.radix_bits ? end_bit - a.shift : plan.radix_bits;
       a.mask = (1u << width) - 1u;
       a.flip_in = is_float(key_type) && pass == 0;
       a.flip_out = is_float(key_type) && pass == plan.places - 1;
@@ -449,14 +493,14 @@ int run_sort(int key_type, const void* keys_in, void* keys_out, const uint32_t* 
       a.skew_flags = header + kSkewWord + pass;
       // signed keys: the top place's high digit bit inverted; descending:
       // every digit complemented within its place
-      a.digit_xor = (pass == plan.places - 1 ? signed_top_xor(key_type, begin_bit, end_bit) : 0u) ^
+      a.digit_xor = (pass == plan.places - 1 ? signed_top_xor(key_type, begin_bit, end_bit, plan.radix_bits) : 0u) ^
                     (is_descending(key_type) ? a.mask : 0u);
-      if (pass >= 8) {
-        // more than 8 passes cannot happen with 8-bit digits of <= 64-bit keys
+      if (pass >= kMaxPlaces) {
+        // more places cannot happen with >= 5-bit digits of <= 64-bit keys
         return OS_ERR_INVALID_ARG;
       }
       const int slot = prof_begin(1, pass, s);
-      const cudaError_t e = launch_binning(plan.key_bits, pairs, plan.cfg, a, s);
+      const cudaError_t e = launch_binning(plan.key_bits, pairs, plan.cfg, a, s, plan.radix_bits);
       prof_end(slot, s);
       if (e != cudaSuccess) return OS_ERR_CUDA;
     }
@@ -739,21 +783,28 @@ int os_sort_batch(int key_type, const void* keys_in, void* keys_out, const uint3
                    end_bit, ws, ws_bytes, stream);
 }
 
-// The caller's binning variant (-1: the process-wide one), or an error.
-static int option_config(const os_sort_options* opt, int* cfg) {
+// The caller's binning variant (-1: the process-wide one) and digit width,
+// or an error.
+static int option_config(const os_sort_options* opt, int* cfg, int* radix_bits) {
   *cfg = -1;
+  *radix_bits = 0;
   if (!opt) return OS_OK;
-  if (opt->reserved != 0 || opt->tile_config < -1 || opt->tile_config >= kTileConfigs) return OS_ERR_INVALID_ARG;
+  if (opt->tile_config < -1 || opt->tile_config >= kTileConfigs) return OS_ERR_INVALID_ARG;
+  if (opt->radix_bits != 0 && (opt->radix_bits < (uint32_t)kMinRadixBits || opt->radix_bits > (uint32_t)kRadixBits))
+    return OS_ERR_INVALID_ARG;
   *cfg = opt->tile_config;
+  if (opt->radix_bits != 0) *radix_bits = (int)opt->radix_bits;
   return OS_OK;
 }
 
 int os_sort_keys_ex(int key_type, const void* keys_in, void* keys_out, uint64_t n, int begin_bit, int end_bit,
                     void* ws, size_t ws_bytes, void* stream, const os_sort_options* opt) {
   int cfg;
-  const int rc = option_config(opt, &cfg);
+  int rb;
+  const int rc = option_config(opt, &cfg, &rb);
   if (rc != OS_OK) return rc;
-  return run_sort(key_type, keys_in, keys_out, nullptr, nullptr, n, begin_bit, end_bit, ws, ws_bytes, stream, cfg);
+  return run_sort(key_type, keys_in, keys_out, nullptr, nullptr, n, begin_bit, end_bit, ws, ws_bytes, stream, cfg,
+                  rb);
 }
 
 int os_sort_pairs_ex(int key_type, const void* keys_in, void* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
@@ -761,17 +812,21 @@ int os_sort_pairs_ex(int key_type, const void* keys_in, void* keys_out, const ui
                      const os_sort_options* opt) {
   if (!vals_in || !vals_out) return OS_ERR_INVALID_ARG;
   int cfg;
-  const int rc = option_config(opt, &cfg);
+  int rb;
+  const int rc = option_config(opt, &cfg, &rb);
   if (rc != OS_OK) return rc;
-  return run_sort(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws, ws_bytes, stream, cfg);
+  return run_sort(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws, ws_bytes, stream, cfg,
+                  rb);
 }
 
 int os_sort_batch_ex(int key_type, const void* keys_in, void* keys_out, const uint32_t* vals_in, uint32_t* vals_out,
                      const uint64_t* seg_offsets, int num_segments, uint64_t n_total, int begin_bit, int end_bit,
                      void* ws, size_t ws_bytes, void* stream, const os_sort_options* opt) {
   int cfg;
-  const int rc = option_config(opt, &cfg);
+  int rb;
+  const int rc = option_config(opt, &cfg, &rb);
   if (rc != OS_OK) return rc;
+  if (rb != 0 && rb != kRadixBits) return OS_ERR_INVALID_ARG;  // batches bin 8-bit digits
   return run_batch(key_type, keys_in, keys_out, vals_in, vals_out, seg_offsets, num_segments, n_total, begin_bit,
                    end_bit, ws, ws_bytes, stream, cfg);
 }
@@ -918,6 +973,21 @@ int os_get_tile_config_bucket(int key_bits, int value_bytes, int bucket) {
       bucket >= kSizeBuckets)
     return -1;
   return get_tile_cfg(key_bits, value_bytes == 4, bucket);
+}
+
+int os_set_radix_bits_bucket(int key_bits, int value_bytes, int bucket, int radix_bits) {
+  if ((key_bits != 32 && key_bits != 64) || (value_bytes != 0 && value_bytes != 4) || bucket < 0 ||
+      bucket >= kSizeBuckets || radix_bits < kMinRadixBits || radix_bits > kRadixBits)
+    return OS_ERR_INVALID_ARG;
+  g_radix_bits[key_bits == 64][value_bytes == 4][bucket].store(radix_bits, std::memory_order_relaxed);
+  return OS_OK;
+}
+
+int os_get_radix_bits_bucket(int key_bits, int value_bytes, int bucket) {
+  if ((key_bits != 32 && key_bits != 64) || (value_bytes != 0 && value_bytes != 4) || bucket < 0 ||
+      bucket >= kSizeBuckets)
+    return -1;
+  return get_radix_bits(key_bits, value_bytes == 4, bucket);
 }
 
 void os_debug_set_lookback_fault(int64_t tile, uint32_t spin_limit) {

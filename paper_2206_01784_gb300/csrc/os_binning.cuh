@@ -94,10 +94,12 @@ struct BinningConfig {
 
 // Lanes of the warp whose digit equals this lane's (valid lanes only): one
 // vote per digit bit (Section 3, WLMS), keeping the lanes that agree on it.
+// RB: bits per digit.
+template <int RB = kRadixBits>
 __device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid, uint32_t valid_mask) {
   uint32_t peers = valid_mask;
 #pragma unroll
-  for (int b = 0; b < kRadixBits; ++b) {
+  for (int b = 0; b < RB; ++b) {
     const bool bit = (d >> b) & 1u;
     const uint32_t v = __ballot_sync(0xFFFFFFFFu, bit);
     peers &= bit ? v : ~v;
@@ -134,7 +136,7 @@ struct TileCtx {
 // key's rank among the keys of the same digit in this warp's part of the tile.
 // msk / cnt: this warp's 256 lane-mask words and 256 running digit counts
 // (separate 32-bit arrays, so random digits spread over all 32 banks).
-template <bool FULL>
+template <bool FULL, int RB = kRadixBits>
 __device__ __forceinline__ uint32_t wlms_rank(uint32_t* msk, uint32_t* cnt, uint32_t d, bool valid, uint32_t lane_bit,
                                               bool smask) {
   // the running count first: its shared-memory round trip overlaps the
@@ -149,7 +151,7 @@ __device__ __forceinline__ uint32_t wlms_rank(uint32_t* msk, uint32_t* cnt, uint
     peers = valid ? msk[d] : 0u;
   } else {
     const uint32_t valid_mask = FULL ? 0xFFFFFFFFu : __ballot_sync(0xFFFFFFFFu, valid);
-    peers = digit_peers(d, valid, valid_mask);
+    peers = digit_peers<RB>(d, valid, valid_mask);
   }
   const uint32_t below = __popc(peers & lanemask_lt());
   __syncwarp();
@@ -230,11 +232,13 @@ constexpr int kLookbackWindow = 4;
 #endif
 constexpr int kRoundEvery = OS_ROUND_EVERY;
 
-template <int KBITS, bool PAIRS, int CFG, int RANK, int FLIP, bool FULL>
+template <int KBITS, bool PAIRS, int CFG, int RANK, int FLIP, bool FULL, int RB>
 __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* smem, const TileCtx& c) {
   using C = BinningConfig<KBITS, PAIRS, CFG>;
   using K = typename C::K;
   constexpr int NT = C::NT, IPT = C::IPT, NW = C::NW;
+  constexpr int R = 1 << RB;  // bins of this pass's digits (the tables keep rows of kRadix)
+  static_assert(R <= kRadix && R <= NT, "one thread per digit");
 
   K* kt = reinterpret_cast<K*>(smem) + c.koff;
   uint32_t* vt = reinterpret_cast<uint32_t*>(smem + C::kbuf_bytes) + c.voff;
@@ -256,7 +260,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
   // the next pass's status counters of this tile start at N
   if (a.status_clear && tid < kRadix)
     for (size_t row = tile; row < a.status_clear_rows; row += a.num_tiles) a.status_clear[row * kRadix + tid] = 0u;
-  const uint32_t bin_offset = tid < kRadix ? __ldg(c.bin_offsets + tid) : 0u;
+  const uint32_t bin_offset = tid < R ? __ldg(c.bin_offsets + tid) : 0u;
   uint32_t* status = a.status + (size_t)tile * kRadix;
   const bool publish = (int64_t)tile != a.fault_tile;
   const bool chain_head = tile == c.chain_first;
@@ -265,7 +269,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
   uint32_t* wmsk = whist + warp * kRadix;
   uint32_t* wc = wcnt + warp * kRadix;
 #pragma unroll
-  for (int i = lane; i < kRadix; i += 32) {
+  for (int i = lane; i < R; i += 32) {
     wmsk[i] = 0u;
     wc[i] = 0u;
   }
@@ -298,13 +302,13 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
   //    whose rounds then ride along the ranking; a tile whose keys share one
   //    digit skips ranking and reorganisation (homogeneous-tile short-circuit)
   uint32_t digit_count = 0;  // thread d < 256: keys of digit d in this tile
-  if (tid < kRadix) {
+  if (tid < R) {
 #pragma unroll
     for (int w = 0; w < NW; ++w) digit_count += wcnt[w * kRadix + tid];
     if (publish)
       st_relaxed_gpu(status + tid, ((chain_head ? kFlagGlobal : kFlagLocal) << kStatusShift) | digit_count);
   }
-  const bool walker = tid < kRadix && !chain_head;
+  const bool walker = tid < R && !chain_head;
   Lookback<kLookbackWindow> lb;
   bool issued = false;
   if (walker) {
@@ -314,16 +318,16 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
     lb.issue(a.status, c.chain_first, tid);
     issued = true;
   }
-  const bool homogeneous = __syncthreads_or(tid < kRadix && digit_count == count) != 0;
+  const bool homogeneous = __syncthreads_or(tid < R && digit_count == count) != 0;
 
   if (homogeneous) {
     if (PAIRS && c.bulk && !mbar_wait_bounded(&mbar[1], 0, kBulkWaitLimit)) atomicOr(a.error, kErrTimeout);
-    if (tid < kRadix) dstart[tid] = 0u;
+    if (tid < R) dstart[tid] = 0u;
   } else {
     // 5. block scan of the counts: tile-local bin starts, and each warp's
     //    counters set to where its first key of each digit goes
-    const uint32_t excl = block_exclusive_sum<NT>(tid < kRadix ? digit_count : 0u, misc);
-    if (tid < kRadix) {
+    const uint32_t excl = block_exclusive_sum<NT>(tid < R ? digit_count : 0u, misc);
+    if (tid < R) {
       uint32_t run = excl;
 #pragma unroll
       for (int w = 0; w < NW; ++w) {
@@ -345,7 +349,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
     for (int i = 0; i < IPT; ++i) {
       const bool valid = FULL || wbase + i * 32 < count;
       const bool smask = RANK == kRankHybrid && (i & 1);
-      const uint32_t p = wlms_rank<FULL>(wmsk, wc, digit_of(key[i], shift, mask, dxor), valid, lane_bit, smask);
+      const uint32_t p = wlms_rank<FULL, RB>(wmsk, wc, digit_of(key[i], shift, mask, dxor), valid, lane_bit, smask);
       if (valid) kt[p] = key[i];
       if (PAIRS) {
         if (i & 1)
@@ -385,7 +389,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
     lb.finish(a, c.chain_first, tid);
     exclusive = lb.exclusive;
   }
-  if (tid < kRadix) {
+  if (tid < R) {
     gbase[tid] = bin_offset + exclusive - dstart[tid];
     // the strip's last tile: where the next strip's keys of this digit start
     if (a.carry_out && tile == a.num_tiles - 1) a.carry_out[tid] = bin_offset + exclusive + digit_count;
@@ -428,7 +432,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
 
 // Kernel front-end: tile id, where the tile sits, staging. SEG selects the
 // segmented (batch) mode, where a.n is the length of the whole key array.
-template <int KBITS, bool PAIRS, int CFG, int RANK, int FLIP, bool SEG>
+template <int KBITS, bool PAIRS, int CFG, int RANK, int FLIP, bool SEG, int RB = kRadixBits>
 __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS, CFG>::NT, BinningConfig<KBITS, PAIRS, CFG>::MIN_BLOCKS)
     binning_kernel(PassArgs a) {
   using C = BinningConfig<KBITS, PAIRS, CFG>;
@@ -518,14 +522,14 @@ __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS, CFG>::NT, BinningC
   const bool ballots = RANK == kRankAdaptive && c.skewed;
   if (c.count == (uint32_t)T) {
     if (ballots)
-      binning_tile<KBITS, PAIRS, CFG, kRankBallot, FLIP, true>(a, smem, c);
+      binning_tile<KBITS, PAIRS, CFG, kRankBallot, FLIP, true, RB>(a, smem, c);
     else
-      binning_tile<KBITS, PAIRS, CFG, R0, FLIP, true>(a, smem, c);
+      binning_tile<KBITS, PAIRS, CFG, R0, FLIP, true, RB>(a, smem, c);
   } else {
     if (ballots)
-      binning_tile<KBITS, PAIRS, CFG, kRankBallot, FLIP, false>(a, smem, c);
+      binning_tile<KBITS, PAIRS, CFG, kRankBallot, FLIP, false, RB>(a, smem, c);
     else
-      binning_tile<KBITS, PAIRS, CFG, R0, FLIP, false>(a, smem, c);
+      binning_tile<KBITS, PAIRS, CFG, R0, FLIP, false, RB>(a, smem, c);
   }
 }
 

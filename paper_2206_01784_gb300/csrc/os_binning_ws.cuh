@@ -601,16 +601,33 @@ cudaError_t launch_binning_ws(const PassArgs& a, cudaStream_t s) {
 
 // ------------------------------------------------------------------ dispatch
 
-template <int KBITS, bool PAIRS, int CFG, int RANK, int FLIP, bool SEG>
+template <int KBITS, bool PAIRS, int CFG, int RANK, int FLIP, bool SEG, int RB = kRadixBits>
 cudaError_t launch_binning_one(const PassArgs& a, cudaStream_t s) {
   using C = BinningConfig<KBITS, PAIRS, CFG>;
   // set on every launch: an idempotent host-side attribute, so concurrent
   // callers on any device need no shared state
-  cudaError_t e = cudaFuncSetAttribute(binning_kernel<KBITS, PAIRS, CFG, RANK, FLIP, SEG>,
+  cudaError_t e = cudaFuncSetAttribute(binning_kernel<KBITS, PAIRS, CFG, RANK, FLIP, SEG, RB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_bytes);
   if (e != cudaSuccess) return e;
-  binning_kernel<KBITS, PAIRS, CFG, RANK, FLIP, SEG><<<a.num_tiles, C::NT, C::smem_bytes, s>>>(a);
+  binning_kernel<KBITS, PAIRS, CFG, RANK, FLIP, SEG, RB><<<a.num_tiles, C::NT, C::smem_bytes, s>>>(a);
   return cudaGetLastError();
+}
+
+// Digits narrower than 8 bits (the digit-width sweep of Section 4, Table 2):
+// tile geometry 0, adaptive ranking, one array; every payload and float
+// transform mode. RB: bits per digit.
+template <int KBITS, int RB>
+cudaError_t launch_binning_rb_t(bool pairs, int flip, const PassArgs& a, cudaStream_t s) {
+  switch ((pairs ? 4 : 0) | (flip & 3)) {
+    case 0: return launch_binning_one<KBITS, false, 0, kRankAdaptive, 0, false, RB>(a, s);
+    case 1: return launch_binning_one<KBITS, false, 0, kRankAdaptive, 1, false, RB>(a, s);
+    case 2: return launch_binning_one<KBITS, false, 0, kRankAdaptive, 2, false, RB>(a, s);
+    case 3: return launch_binning_one<KBITS, false, 0, kRankAdaptive, 3, false, RB>(a, s);
+    case 4: return launch_binning_one<KBITS, true, 0, kRankAdaptive, 0, false, RB>(a, s);
+    case 5: return launch_binning_one<KBITS, true, 0, kRankAdaptive, 1, false, RB>(a, s);
+    case 6: return launch_binning_one<KBITS, true, 0, kRankAdaptive, 2, false, RB>(a, s);
+    default: return launch_binning_one<KBITS, true, 0, kRankAdaptive, 3, false, RB>(a, s);
+  }
 }
 
 template <int KBITS, bool PAIRS, int FLIP, int RANK, bool SEG>

@@ -32,9 +32,10 @@ constexpr int kHistVec = 4;  // 16-byte loads in flight per thread per step
 
 template <int KBITS>
 struct HistLayout {
-  static constexpr int P = KBITS / 8;              // most places a key can have
+  static constexpr int P = KBITS / 8;              // places of 8-bit digits a key has
+  static constexpr int kMaxP = KBITS / 5;          // most places: 5-bit digits (rounded up below)
   static constexpr int kCopies = KBITS == 32 ? 32 : 16;
-  static constexpr int kEntries = P * kRadix;
+  static constexpr int kEntries = P * kRadix;      // counters per copy: places x bins, for any digit width
   static constexpr size_t smem_bytes = (size_t)kEntries * kCopies * 4;
 };
 
@@ -82,8 +83,12 @@ __global__ void __launch_bounds__(kHistThreads, 1) histogram_kernel(HistArgs a) 
   }
   __syncthreads();
 
-  const uint32_t last_mask = (1u << (a.end_bit - (a.begin_bit + 8 * (p - 1)))) - 1u;
-  // this lane's copy: counter (place, digit) at word ((place * 256 + digit) * C + copy)
+  // digits of rb bits (8 in the FULL mode): place i covers bits
+  // [begin + rb*i, +rb), the last one possibly narrower; counter (place,
+  // digit) of this lane's copy at word ((place * 2^rb + digit) * C + copy)
+  const int rb = FULL ? 8 : a.radix_bits;
+  const int nbin = 1 << rb;
+  const uint32_t last_mask = (1u << (a.end_bit - (a.begin_bit + rb * (p - 1)))) - 1u;
   uint32_t* mine = sh + (tid & 31) % C;
   const uint32_t top_xor = a.top_xor;
   auto count_key = [&](K k) {
@@ -96,11 +101,11 @@ __global__ void __launch_bounds__(kHistThreads, 1) histogram_kernel(HistArgs a) 
       }
     } else {
 #pragma unroll
-      for (int pl = 0; pl < P; ++pl) {
+      for (int pl = 0; pl < L::kMaxP + 1; ++pl) {
         if (pl < p) {
-          const uint32_t d =
-              digit_of(o, a.begin_bit + 8 * pl, pl == p - 1 ? last_mask : 0xFFu, pl == p - 1 ? top_xor : 0u);
-          atomicAdd(mine + (pl * kRadix + d) * C, 1u);
+          const uint32_t d = digit_of(o, a.begin_bit + rb * pl, pl == p - 1 ? last_mask : (uint32_t)nbin - 1u,
+                                      pl == p - 1 ? top_xor : 0u);
+          atomicAdd(mine + (pl * nbin + d) * C, 1u);
         }
       }
     }
@@ -168,11 +173,12 @@ __global__ void __launch_bounds__(kHistThreads, 1) histogram_kernel(HistArgs a) 
   // add the block's copies of every counter (each lane starts at a different
   // copy, so a warp's reads hit distinct banks) and flush to global memory
   const int lane = tid & 31;
-  for (int e = tid; e < p * kRadix; e += kHistThreads) {
+  for (int e = tid; e < p * nbin; e += kHistThreads) {
     uint32_t sum = 0;
 #pragma unroll 8
     for (int c = 0; c < C; ++c) sum += sh[e * C + ((c + lane) % C)];
-    if (sum) atomicAdd(a.hist + e, sum);
+    // global histograms keep rows of kRadix words per place
+    if (sum) atomicAdd(a.hist + (e >> rb) * kRadix + (e & (nbin - 1)), sum);
   }
 
   // Phase 2 in the last block to finish: exclusive sum of each place's counts.
@@ -185,7 +191,7 @@ __global__ void __launch_bounds__(kHistThreads, 1) histogram_kernel(HistArgs a) 
   for (int pl = 0; pl < p; ++pl) {
     // a descending sort bins by the complement of each digit within its
     // place: count of complemented digit t = count of digit t ^ mask
-    const uint32_t pmask = pl == p - 1 ? last_mask : 0xFFu;
+    const uint32_t pmask = pl == p - 1 ? last_mask : (uint32_t)nbin - 1u;
     const uint32_t src = a.descending ? (tid ^ pmask) : (uint32_t)tid;
     const uint32_t c = (tid < kRadix && (uint32_t)tid <= pmask) ? ld_relaxed_gpu(a.hist + pl * kRadix + src) : 0u;
     const uint32_t excl = block_exclusive_sum<kHistThreads>(c, scan_tmp);
@@ -203,22 +209,18 @@ __global__ void __launch_bounds__(kHistThreads, 1) histogram_kernel(HistArgs a) 
 template <int KBITS, bool FULL, bool FLIP>
 cudaError_t launch_hist_mode(const HistArgs& a, int grid, cudaStream_t s) {
   constexpr size_t bytes = HistLayout<KBITS>::smem_bytes;
-  static int configured_device = -1;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (configured_device != dev) {
-    cudaError_t e = cudaFuncSetAttribute(histogram_kernel<KBITS, FULL, FLIP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    configured_device = dev;
-  }
+  // set on every launch: an idempotent host-side attribute, so concurrent
+  // callers on any device need no shared state
+  cudaError_t e = cudaFuncSetAttribute(histogram_kernel<KBITS, FULL, FLIP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
   histogram_kernel<KBITS, FULL, FLIP><<<grid, kHistThreads, bytes, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int KBITS>
 cudaError_t launch_hist_t(const HistArgs& a, int grid, cudaStream_t s) {
-  const bool full = a.begin_bit == 0 && a.end_bit == KBITS && a.num_places == KBITS / 8;
+  const bool full = a.begin_bit == 0 && a.end_bit == KBITS && a.num_places == KBITS / 8 && a.radix_bits == 8;
   if (full) return a.flip ? launch_hist_mode<KBITS, true, true>(a, grid, s) : launch_hist_mode<KBITS, true, false>(a, grid, s);
   return a.flip ? launch_hist_mode<KBITS, false, true>(a, grid, s) : launch_hist_mode<KBITS, false, false>(a, grid, s);
 }

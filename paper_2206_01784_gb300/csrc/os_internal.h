@@ -14,9 +14,10 @@ struct HistArgs {
   uint64_t n;
   int flip;                  // float keys: apply the sign-flip before taking digits
   int num_places;            // p
-  int begin_bit;             // place i covers bits [begin_bit + 8i, min(+8, end_bit))
+  int radix_bits;            // d: place i covers bits [begin_bit + d*i, min(+d, end_bit)); 5..8
+  int begin_bit;
   int end_bit;
-  uint32_t* hist;            // [p][256] zeroed by the caller (device)
+  uint32_t* hist;            // [p][256] zeroed by the caller (device); 2^d bins used per row
   uint32_t* offsets;         // [p][256] written by the last block (device)
   uint32_t* done_counter;    // zeroed by the caller (device)
   uint32_t* clear;           // words to zero on the way (status slab of pass 0), may be null
@@ -125,6 +126,7 @@ int sort_on_workspace(int key_type, const void* keys_in, void* keys_out, const u
 
 cudaError_t launch_histogram(int key_bits, const HistArgs& a, int num_sms, cudaStream_t s);
 // Launches variant cfg of the binning kernel (the variant a plan was made with).
-cudaError_t launch_binning(int key_bits, bool pairs, int cfg, const PassArgs& a, cudaStream_t s);
+cudaError_t launch_binning(int key_bits, bool pairs, int cfg, const PassArgs& a, cudaStream_t s,
+                           int radix_bits = 8);
 
 }  // namespace onesweep

@@ -50,8 +50,9 @@ class LaunchTime(ctypes.Structure):
 
 
 class SortOptions(ctypes.Structure):
-    """os_sort_options: the binning variant of one call (-1: process-wide)."""
-    _fields_ = [("tile_config", ctypes.c_int), ("reserved", ctypes.c_uint32)]
+    """os_sort_options: the binning variant of one call (-1: process-wide) and
+    its bits per digit place (0: the default, 8)."""
+    _fields_ = [("tile_config", ctypes.c_int), ("radix_bits", ctypes.c_uint32)]
 
 
 _lib = None
@@ -124,6 +125,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.os_set_tile_config_bucket.argtypes = [i32, i32, i32, i32]
     lib.os_get_tile_config_bucket.restype = i32
     lib.os_get_tile_config_bucket.argtypes = [i32, i32, i32]
+    lib.os_set_radix_bits_bucket.restype = i32
+    lib.os_set_radix_bits_bucket.argtypes = [i32, i32, i32, i32]
+    lib.os_get_radix_bits_bucket.restype = i32
+    lib.os_get_radix_bits_bucket.argtypes = [i32, i32, i32]
     lib.os_mlp_param_count.restype = i32
     lib.os_mlp_param_count.argtypes = [i32, i32]
     lib.os_mlp_forward.restype = i32
@@ -165,26 +170,30 @@ def os_sort_pairs(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, 
                                     ws_bytes, stream))
 
 
-def _options(tile_config):
-    return None if tile_config is None else ctypes.byref(SortOptions(int(tile_config), 0))
+def _options(tile_config, radix_bits=None):
+    if tile_config is None and radix_bits is None:
+        return None
+    return ctypes.byref(SortOptions(-1 if tile_config is None else int(tile_config),
+                                    0 if radix_bits is None else int(radix_bits)))
 
 
 def os_sort_keys_ex(key_type, keys_in, keys_out, n, begin_bit, end_bit, ws, ws_bytes, stream,
-                    tile_config=None) -> int:
+                    tile_config=None, radix_bits=None) -> int:
     return int(load().os_sort_keys_ex(key_type, keys_in, keys_out, n, begin_bit, end_bit, ws, ws_bytes, stream,
-                                      _options(tile_config)))
+                                      _options(tile_config, radix_bits)))
 
 
 def os_sort_pairs_ex(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws, ws_bytes, stream,
-                     tile_config=None) -> int:
+                     tile_config=None, radix_bits=None) -> int:
     return int(load().os_sort_pairs_ex(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws,
-                                       ws_bytes, stream, _options(tile_config)))
+                                       ws_bytes, stream, _options(tile_config, radix_bits)))
 
 
 def os_sort_batch_ex(key_type, keys_in, keys_out, vals_in, vals_out, seg_offsets, num_segments, n_total, begin_bit,
-                     end_bit, ws, ws_bytes, stream, tile_config=None) -> int:
+                     end_bit, ws, ws_bytes, stream, tile_config=None, radix_bits=None) -> int:
     return int(load().os_sort_batch_ex(key_type, keys_in, keys_out, vals_in, vals_out, seg_offsets, num_segments,
-                                       n_total, begin_bit, end_bit, ws, ws_bytes, stream, _options(tile_config)))
+                                       n_total, begin_bit, end_bit, ws, ws_bytes, stream,
+                                       _options(tile_config, radix_bits)))
 
 
 def os_sort_batch_workspace_bytes(key_type: int, n_total: int, num_segments: int, value_bytes: int, begin_bit: int,
@@ -283,6 +292,14 @@ def os_set_tile_config_bucket(key_bits: int, value_bytes: int, bucket: int, cfg:
     return int(load().os_set_tile_config_bucket(key_bits, value_bytes, bucket, cfg))
 
 
+def os_set_radix_bits_bucket(key_bits: int, value_bytes: int, bucket: int, radix_bits: int) -> int:
+    return int(load().os_set_radix_bits_bucket(key_bits, value_bytes, bucket, radix_bits))
+
+
+def os_get_radix_bits_bucket(key_bits: int, value_bytes: int, bucket: int) -> int:
+    return int(load().os_get_radix_bits_bucket(key_bits, value_bytes, bucket))
+
+
 def os_get_tile_config_bucket(key_bits: int, value_bytes: int, bucket: int) -> int:
     return int(load().os_get_tile_config_bucket(key_bits, value_bytes, bucket))
 
@@ -368,8 +385,9 @@ def _with_order(kt: int, descending: bool) -> int:
 
 
 def sort_keys(keys, begin_bit: int = 0, end_bit: int | None = None, key_type=None, out=None, ws=None,
-              stream=None, descending: bool = False):
-    """Stable ascending (or descending) sort of a 1-D CUDA tensor of keys; returns the sorted keys."""
+              stream=None, descending: bool = False, radix_bits: int | None = None):
+    """Stable ascending (or descending) sort of a 1-D CUDA tensor of keys;
+    returns the sorted keys. radix_bits: bits per digit place (None: 8)."""
     torch = _torch()
     kt = key_type_of(keys, key_type)
     end_bit = KEY_BITS[kt] if end_bit is None else end_bit
@@ -378,14 +396,15 @@ def sort_keys(keys, begin_bit: int = 0, end_bit: int | None = None, key_type=Non
     n = keys.numel()
     out = torch.empty_like(keys) if out is None else out
     ws = workspace(kt, n, 0, begin_bit, end_bit, keys.device) if ws is None else ws
-    _check(os_sort_keys(kt, keys.data_ptr(), out.data_ptr(), n, begin_bit, end_bit, ws.data_ptr(), ws.numel(),
-                        _stream_ptr(stream)), "os_sort_keys")
+    _check(os_sort_keys_ex(kt, keys.data_ptr(), out.data_ptr(), n, begin_bit, end_bit, ws.data_ptr(), ws.numel(),
+                           _stream_ptr(stream), radix_bits=radix_bits), "os_sort_keys")
     return out
 
 
 def sort_pairs(keys, values, begin_bit: int = 0, end_bit: int | None = None, key_type=None, keys_out=None,
-               values_out=None, ws=None, stream=None, descending: bool = False):
-    """Stable ascending (or descending) sort of (key, uint32 value) pairs; returns (keys, values)."""
+               values_out=None, ws=None, stream=None, descending: bool = False, radix_bits: int | None = None):
+    """Stable ascending (or descending) sort of (key, uint32 value) pairs;
+    returns (keys, values). radix_bits: bits per digit place (None: 8)."""
     torch = _torch()
     kt = key_type_of(keys, key_type)
     end_bit = KEY_BITS[kt] if end_bit is None else end_bit
@@ -398,8 +417,9 @@ def sort_pairs(keys, values, begin_bit: int = 0, end_bit: int | None = None, key
     keys_out = torch.empty_like(keys) if keys_out is None else keys_out
     values_out = torch.empty_like(values) if values_out is None else values_out
     ws = workspace(kt, n, 4, begin_bit, end_bit, keys.device) if ws is None else ws
-    _check(os_sort_pairs(kt, keys.data_ptr(), keys_out.data_ptr(), values.data_ptr(), values_out.data_ptr(), n,
-                         begin_bit, end_bit, ws.data_ptr(), ws.numel(), _stream_ptr(stream)), "os_sort_pairs")
+    _check(os_sort_pairs_ex(kt, keys.data_ptr(), keys_out.data_ptr(), values.data_ptr(), values_out.data_ptr(), n,
+                            begin_bit, end_bit, ws.data_ptr(), ws.numel(), _stream_ptr(stream),
+                            radix_bits=radix_bits), "os_sort_pairs")
     return keys_out, values_out
 
 

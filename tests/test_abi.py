@@ -161,8 +161,18 @@ def test_size_buckets_and_tuning_table_roundtrip(tmp_path):
         assert autotune.load(str(p)) == table
         assert osw.os_set_tile_config_bucket(32, 4, nb, 0) == osw.OS_ERR_INVALID_ARG
         assert osw.os_get_tile_config_bucket(32, 4, -1) == -1
+        # the digit width per bucket: 8 until set, 5-8 accepted
+        assert osw.os_get_radix_bits_bucket(32, 0, 2) == 8
+        autotune.apply({(32, 0, 2): {"cfg": 4, "radix_bits": 6}})
+        assert osw.os_get_radix_bits_bucket(32, 0, 2) == 6
+        for bad in (0, 4, 9):
+            assert osw.os_set_radix_bits_bucket(32, 0, 2, bad) == osw.OS_ERR_INVALID_ARG
+        assert osw.os_set_radix_bits_bucket(48, 0, 2, 6) == osw.OS_ERR_INVALID_ARG
+        assert osw.os_get_radix_bits_bucket(32, 0, nb) == -1
+        assert autotune.candidates() == [(c, 8) for c in range(osw.os_num_tile_configs())] + [(4, 5), (4, 6), (4, 7)]
     finally:
         autotune.apply(saved)
+    assert osw.os_get_radix_bits_bucket(32, 0, 2) == 8
 
 
 def test_host_api_validation_without_gpu():

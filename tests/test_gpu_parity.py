@@ -306,8 +306,10 @@ def test_autotune_small_buckets_keeps_results():
         table = autotune.tune(key_bits=(32,), value_bytes=(4,), buckets=(0, 1), steps=2, warmup=1)
         for b in (0, 1):
             rec = table[(32, 4, b)]
-            assert len(rec["ms"]) == osw.os_num_tile_configs() and all(t > 0 for t in rec["ms"])
+            # every variant with 8-bit digits, variant 4 with 5-, 6- and 7-bit digits
+            assert len(rec["ms"]) == osw.os_num_tile_configs() + 3 and all(t > 0 for t in rec["ms"].values())
             assert osw.os_get_tile_config_bucket(32, 4, b) == rec["cfg"]
+            assert osw.os_get_radix_bits_bucket(32, 4, b) == rec["radix_bits"]
         n = 300_007
         keys = make_keys("u32", "and2", n, seed=99)
         vals = workload.iota_u32(n)
