@@ -68,7 +68,8 @@ constexpr int kMaxPlaces = 16;  // 64-bit keys in 5-bit digits: 13 places
 // Binning kernel variants: tile geometry (4) x digit-ranking method (3);
 // variant v uses geometry v % 4 and ranking v / 4 (0: one ballot per digit
 // bit; 1: adaptive - ballots where the place is skewed, else the hybrid;
-// 2: hybrid - ballots and shared-memory lane masks alternating by batch).
+// 2: hybrid - shared-memory lane masks on two of every three batches, ballots
+// on the third).
 // Geometries 0-2 run one block per tile; geometry 3 is the persistent,
 // warp-specialised kernel (os_binning_ws.cuh), for single arrays only.
 constexpr int kGeometries = 4;

@@ -345,7 +345,7 @@ __device__ __forceinline__ void ws_rank_tile(const PassArgs& a, unsigned char* s
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       const bool valid = FULL || wbase + i * 32 < count;
-      const bool smask = RANK == kRankHybrid && (i & 1);
+      const bool smask = RANK == kRankHybrid && hybrid_uses_masks(i);
       const uint32_t r = wlms_rank<FULL>(wmsk, wc, digit_of(key[i], shift, mask, dxor), valid, lane_bit, smask);
       if (i & 1)
         rank2[i / 2] |= r << 16;
