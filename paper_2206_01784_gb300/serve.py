@@ -63,6 +63,7 @@ class Request:
     done: float = math.nan    # seconds after the start (device completion)
     batch: int = -1           # batch id
     segment: int = -1         # its segment within the batch
+    priority: float = math.nan  # admission priority (lower first), set once when first seen
 
 
 class Arena:
@@ -118,9 +119,10 @@ class Admission:
     group already holding its reservation in the arena (``reservations``)."""
 
     def __init__(self, arena: Arena, workspace_bytes, max_batch_keys: int = 1 << 30, order=None):
-        """order: None for first-come-first-served, or a callable mapping the
-        arrived waiting requests to {id(request): priority} (lower first), as
-        learned.CostModel.priority does with predicted device times."""
+        """order: None for first-come-first-served, or a callable mapping
+        requests to {id(request): priority} (lower first), as
+        learned.CostModel.priority does with predicted device times. It is
+        called once per request, with the requests first seen at a tick."""
         self.arena = arena
         self.workspace_bytes = workspace_bytes
         self.max_batch_keys = max_batch_keys
@@ -150,8 +152,14 @@ class Admission:
         admitted = 0
         arrived = [r for r in self.waiting if r.arrival <= now]
         if self.order is not None and arrived:
-            prio = self.order(arrived)
-            arrived = sorted(arrived, key=lambda r: (prio[id(r)], r.arrival, r.rid))
+            # a request's priority is computed once, when it is first seen (the
+            # loop is latency-bound host code: nothing per request per tick)
+            new = [r for r in arrived if math.isnan(r.priority)]
+            if new:
+                prio = self.order(new)
+                for r in new:
+                    r.priority = float(prio[id(r)])
+            arrived.sort(key=lambda r: (r.priority, r.arrival, r.rid))
         keys_in_group: dict[str, int] = {}
         for r in arrived:
             g = groups.setdefault(r.key_type, [])

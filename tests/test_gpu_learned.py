@@ -72,9 +72,24 @@ def test_training_fits_measured_sort_times():
     assert np.median(np.abs(np.exp(pred - T) - 1.0)) < 0.3
 
 
+def test_batched_costs_fit_and_host_predictions_match_the_kernel():
+    _dev()
+    X, T = learned.collect_batched(sizes_log2=range(10, 23, 2), reps=2)
+    # a request's share of a batch grows with its keys, and 64-bit keys cost more
+    t = np.exp(T).reshape(3, -1)
+    assert np.all(np.diff(t[:, 2:], axis=1) > 0)
+    assert np.all(t[1, 3:] > 1.5 * t[0, 3:])
+    model = learned.CostModel(hidden=32, seed=0)
+    hist = model.fit(X, T, steps=2500, lr=3e-3)
+    assert hist[-1] < 0.05 * hist[0]
+    # the service evaluates the network on the host from a parameter copy:
+    # the same function as the forward kernel, to float32 rounding
+    assert np.allclose(model.predict_log_ms_host(X), model.predict_log_ms(X), atol=1e-4)
+
+
 def test_shortest_predicted_first_beats_fifo_on_a_burst():
     _dev()
-    X, T = learned.collect(sizes_log2=range(10, 23, 2), reps=2)
+    X, T = learned.collect_batched(sizes_log2=range(10, 23, 2), reps=2)
     model = learned.CostModel(hidden=32, seed=0)
     model.fit(X, T, steps=2500, lr=3e-3)
     # a 256 MB budget and 1M-key batches serialise the burst, so the order of
@@ -94,6 +109,8 @@ def test_shortest_predicted_first_beats_fifo_on_a_burst():
         runs["sjf"].append(srv.run(burst(), realtime=False, max_batch_keys=1 << 20, order=model.priority))
     fifo = min(runs["fifo"], key=lambda r: r["mean_ms"])
     sjf = min(runs["sjf"], key=lambda r: r["mean_ms"])
+    print(f"burst: fifo mean {fifo['mean_ms']:.2f} p50 {fifo['p50_ms']:.2f}; "
+          f"predicted-shortest-first mean {sjf['mean_ms']:.2f} p50 {sjf['p50_ms']:.2f} ms")
     # the same work, but small requests no longer wait behind large ones
     assert sjf["keys"] == fifo["keys"]
     assert sjf["mean_ms"] < 0.85 * fifo["mean_ms"], (sjf["mean_ms"], fifo["mean_ms"])
