@@ -302,6 +302,7 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
   for (int i = 0; i < IPT; ++i)
     if (FULL || wbase + i * 32 < count) atomicAdd(wc + digit_of(key[i], shift, mask, dxor), 1u);
   const uint32_t d0 = digit_of(load_transform<FLIP>(kt[0]), shift, mask, dxor);
+  if (tid == 0) misc[NW] = 0u;  // set below by the digit that holds every key, if one does
   __syncthreads();
 
   // 4. tile digit counts: publish L now, and start the look-back (step 6),
@@ -324,15 +325,29 @@ __device__ __forceinline__ void binning_tile(const PassArgs& a, unsigned char* s
     lb.issue(a.status, c.chain_first, tid);
     issued = true;
   }
-  const bool homogeneous = __syncthreads_or(tid < R && digit_count == count) != 0;
+  // block scan of the counts (a warp scan, one barrier, the lower warps'
+  // totals), which also tells whether every key has the same digit
+  static_assert(NW < 64, "scan scratch");
+  uint32_t incl = tid < R ? digit_count : 0u;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) misc[warp] = incl;
+  if (tid < R && digit_count == count) misc[NW] = 1u;
+  __syncthreads();
+  const bool homogeneous = misc[NW] != 0u;
 
   if (homogeneous) {
     if (PAIRS && c.bulk && !mbar_wait_bounded(&mbar[1], 0, kBulkWaitLimit)) atomicOr(a.error, kErrTimeout);
     if (tid < R) dstart[tid] = 0u;
   } else {
-    // 5. block scan of the counts: tile-local bin starts, and each warp's
-    //    counters set to where its first key of each digit goes
-    const uint32_t excl = block_exclusive_sum<NT>(tid < R ? digit_count : 0u, misc);
+    // 5. tile-local bin starts, and each warp's counters set to where its
+    //    first key of each digit goes
+    uint32_t excl = incl - (tid < R ? digit_count : 0u);
+    for (int w = 0; w < NW; ++w)
+      if (w < warp) excl += misc[w];
     if (tid < R) {
       uint32_t run = excl;
 #pragma unroll
