@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kSegHistThreads) batch_histogram_kernel(BatchA
     const uint32_t c = (tid < kRadix && (uint32_t)tid <= pmask) ? ld_relaxed_gpu(gh + pl * kRadix + src) : 0u;
     const uint32_t excl = block_exclusive_sum<kSegHistThreads>(c, scan_tmp);
     if (tid < kRadix) go[pl * kRadix + tid] = excl;
-    const int skewed = __syncthreads_or(tid < kRadix && (uint64_t)c * 16u > len);
+    const int skewed = __syncthreads_or(tid < kRadix && (uint64_t)c * kSkewDivisor > len);
     if (tid == 0) b.seg_skew[(size_t)seg * p + pl] = skewed ? 1u : 0u;
   }
 }

@@ -21,6 +21,10 @@ constexpr uint32_t kFlagNotReady = 0u;  // N
 constexpr uint32_t kFlagLocal = 1u;     // L: this tile's digit count
 constexpr uint32_t kFlagGlobal = 2u;    // G: inclusive prefix over tiles 0..t
 
+// A digit place is skewed (its binning pass ranks with ballots only) when one
+// digit holds more than 1/kSkewDivisor of the keys.
+constexpr uint32_t kSkewDivisor = 8;
+
 // Bits of the workspace's device status word.
 constexpr uint32_t kErrTimeout = 1u;
 

@@ -198,10 +198,11 @@ __global__ void __launch_bounds__(kHistThreads, 1) histogram_kernel(HistArgs a) 
     if (tid < kRadix) a.offsets[pl * kRadix + tid] = excl;
     // (every read of this place's counts is before the scan's barriers)
     if (a.descending && tid < kRadix) a.hist[pl * kRadix + tid] = c;
-    // a place where one digit holds over 1/16 of the keys is "skewed": its
+    // a place where one digit holds over 1/8 of the keys is "skewed": its
     // binning pass ranks with ballots, which do not slow down when many lanes
-    // share a digit
-    const int skewed = __syncthreads_or(tid < kRadix && (uint64_t)c * 16u > a.n);
+    // share a digit (measured on GB300: at ~10 % in one digit the lane masks
+    // are still faster, at ~34 % the ballots are)
+    const int skewed = __syncthreads_or(tid < kRadix && (uint64_t)c * kSkewDivisor > a.n);
     if (tid == 0 && a.skew) a.skew[pl] = skewed ? 1u : 0u;
   }
 }
