@@ -61,7 +61,10 @@ def run_batch(kt, keys, sizes, pairs, begin=0, end=None):
 
 def edge_sizes(kt, pairs):
     cap = 4096 if KB[kt] == 32 else 2048  # one-block capacity
-    t = osw.os_tile_config_keys(KB[kt], 4 if pairs else 0, osw.os_get_tile_config(KB[kt], 4 if pairs else 0))
+    cfg = osw.os_get_tile_config(KB[kt], 4 if pairs else 0)
+    if cfg % 4 == 3:  # the persistent geometry serves single arrays; a batch runs geometry 0
+        cfg -= 3
+    t = osw.os_tile_config_keys(KB[kt], 4 if pairs else 0, cfg)
     return [0, 1, 2, 31, 33, cap - 1, cap, cap + 1, 0, t - 1, t, t + 1, 3 * t + 7, 1000, 0, 5, 2 * cap + 3]
 
 
