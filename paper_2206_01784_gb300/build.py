@@ -63,7 +63,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
             sys.stderr.write(res.stdout + res.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, sources()))
     tmp = LIB_PATH + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]

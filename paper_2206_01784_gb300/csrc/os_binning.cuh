@@ -231,6 +231,10 @@ struct Lookback {
   }
 };
 constexpr int kLookbackWindow = 4;
+// Tiles ahead whose keys (and values) a starting block prefetches into L2
+// (measured at 2^28 keys on GB300: 48, 144 and 384 tiles ahead all shorten a
+// pass by about 1 %; the tile's own staging copy then waits less).
+constexpr uint32_t kPrefetchTiles = 48;
 // Ranking batches between two look-back rounds: about one L2 round trip of
 // ranking work, so a round's reads have come back when it is consumed.
 #ifndef OS_ROUND_EVERY
@@ -522,6 +526,14 @@ __global__ void __launch_bounds__(BinningConfig<KBITS, PAIRS, CFG>::NT, BinningC
           bulk_copy_g2s(vbuf, a.vals_in + vs, vbytes, &mbar[1]);
         }
       }
+    }
+    // the tile kPrefetchTiles ahead starts well within one block lifetime:
+    // bring it into L2 now, so its staging copy reads L2 instead of DRAM
+    if (!SEG && a.use_bulk && tile + kPrefetchTiles < a.num_tiles &&
+        (uint64_t)(tile + kPrefetchTiles + 1) * T <= a.n) {
+      const size_t first = (size_t)(tile + kPrefetchTiles) * T;
+      bulk_prefetch_l2(static_cast<const K*>(a.keys_in) + first, (uint32_t)(T * sizeof(K)));
+      if (PAIRS) bulk_prefetch_l2(a.vals_in + first, (uint32_t)T * 4u);
     }
     s_ctx = c;
   }
