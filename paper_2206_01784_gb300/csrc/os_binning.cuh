@@ -175,10 +175,20 @@ __device__ __forceinline__ uint32_t wlms_rank(uint32_t* msk, uint32_t* cnt, uint
 // again - until a G counter or the chain's first tile is reached, and then
 // publishes this tile's (G, inclusive prefix). A round may stay in flight
 // while the block does other work between issue() and consume().
+//
+// Beyond the paper's N/L/G protocol, a walk that has passed m preceding tiles
+// but not yet reached a G counter publishes (A, m + 1, sum of the m + 1
+// counts through this tile) in place of its L: a later walk that reads it adds
+// the whole span's count and continues below it, instead of reading the m + 1
+// tiles one by one. Each value a walk adds is the exact sum of a contiguous
+// span ending where it reads, and the spans it adds are disjoint and
+// adjacent, so the prefix is the paper's; a word only ever goes N -> L ->
+// A... -> G, written by its own tile's walker.
 template <int W>
 struct Lookback {
   uint32_t s[W];       // counters of the round in flight
   uint32_t left;       // preceding tiles of the chain not yet accumulated
+  uint32_t total;      // preceding tiles of the chain
   uint32_t exclusive;  // sum of the accumulated counters
   uint32_t own;        // this tile's count of the digit
   uint32_t* mine;      // this tile's counter of the digit (null: publish nothing)
@@ -186,12 +196,20 @@ struct Lookback {
 
   __device__ __forceinline__ void start(uint32_t tile, uint32_t chain_first) {
     left = tile - chain_first;
+    total = left;
     exclusive = 0u;
     done = left == 0u;
   }
   // (G, exclusive + own): the inclusive prefix of the digit through this tile
   __device__ __forceinline__ void publish_global() {
     if (mine) st_relaxed_gpu(mine, (kFlagGlobal << kStatusShift) | (exclusive + own));
+  }
+  // (A, span, sum): this tile and the total - left predecessors passed so far
+  __device__ __forceinline__ void publish_aggregate() {
+    const uint32_t span = total - left + 1u;
+    const uint32_t sum = exclusive + own;
+    if (mine && span <= kAggMaxSpan && sum <= kAggValueMask)
+      st_relaxed_gpu(mine, (kFlagAggregate << kStatusShift) | ((span - 1u) << kAggSpanShift) | sum);
   }
   // reads tiles chain_first + left - 1, chain_first + left - 2, ...
   __device__ __forceinline__ void issue(const uint32_t* status, uint32_t chain_first, int digit) {
@@ -201,16 +219,27 @@ struct Lookback {
                                 : (kFlagGlobal << kStatusShift);
   }
   __device__ __forceinline__ void consume() {
+    const uint32_t left0 = left;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       if (done) break;
       const uint32_t flag = s[w] >> kStatusShift;
       if (flag == kFlagNotReady) break;  // read this tile again next round
+      if (flag == kFlagAggregate) {
+        // a whole span ending at this tile; the round's next rows lie inside it
+        exclusive += s[w] & kAggValueMask;
+        left -= ((s[w] >> kAggSpanShift) & (kAggMaxSpan - 1u)) + 1u;
+        if (left == 0u) done = true;
+        break;
+      }
       exclusive += s[w] & kValueMask;
       --left;
       if (flag == kFlagGlobal || left == 0u) done = true;
     }
-    if (done) publish_global();
+    if (done)
+      publish_global();
+    else if (left != left0)
+      publish_aggregate();
   }
   // rounds until the walk ends, each waiting for its reads; a wait past the
   // poll limit records a timeout and still publishes (the successors' walks

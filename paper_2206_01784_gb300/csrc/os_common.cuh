@@ -20,6 +20,14 @@ constexpr uint32_t kValueMask = (1u << kStatusShift) - 1u;
 constexpr uint32_t kFlagNotReady = 0u;  // N
 constexpr uint32_t kFlagLocal = 1u;     // L: this tile's digit count
 constexpr uint32_t kFlagGlobal = 2u;    // G: inclusive prefix over tiles 0..t
+// A: the sum of the counts of a span of tiles ending at this one (this tile and
+// the predecessors its walk has already passed), so a later walk skips the
+// whole span in one read. The value then takes the low 24 bits and span - 1
+// the next 6 (a span covers at most 64 tiles of at most 6144 keys).
+constexpr uint32_t kFlagAggregate = 3u;
+constexpr uint32_t kAggSpanShift = 24;
+constexpr uint32_t kAggValueMask = (1u << kAggSpanShift) - 1u;
+constexpr uint32_t kAggMaxSpan = 64;
 
 // A digit place is skewed (its binning pass ranks with ballots only) when one
 // digit holds more than 1/kSkewDivisor of the keys.
