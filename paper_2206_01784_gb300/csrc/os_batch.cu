@@ -20,11 +20,13 @@
 
 namespace onesweep {
 
+int ws_grid(uint32_t num_tiles);  // min(num_tiles, SMs of the current device)
+
 namespace {
 
 constexpr int kPlanThreads = 1024;
-constexpr int kSegHistThreads = 512;
-constexpr int kSegHistKpt = 8;  // keys per thread per step of the segment histogram
+constexpr int kSegHistThreads = 1024;
+constexpr int kSegHistVec = 4;  // 16-byte loads in flight per thread per step of the segment histogram
 
 __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(BatchArgs b) {
   __shared__ uint32_t tmp_t[kPlanThreads / 32 + 1];
@@ -76,15 +78,41 @@ __global__ void __launch_bounds__(kPlanThreads) batch_plan_kernel(BatchArgs b) {
   }
 }
 
+// Per-segment digit histograms of every place (Section 3, "Upfront histogram
+// kernel", per segment). One persistent 1024-thread block per SM takes a
+// contiguous range of the batch's work items (chunks of hist_chunk keys, a
+// segment's items consecutive), so a block mostly meets whole runs of one
+// segment's items: it counts them into block-private histograms and flushes
+// them to the segment's global histograms with global atomics once per run.
+// As in the single-array histogram kernel, each lane owns its own copy of the
+// counters, laid out in its own shared-memory bank (counter e of copy c at
+// word e * C + c), so every warp-wide atomic is one conflict-free wavefront
+// and skewed keys cost no more than uniform ones; keys are read with 128-bit
+// streaming loads (the unaligned head and tail of a chunk one key per
+// thread). The flush that completes a segment's items takes the segment's
+// exclusive sums (its bin offsets) and skewed-place flags.
 template <int KBITS>
-__global__ void __launch_bounds__(kSegHistThreads) batch_histogram_kernel(BatchArgs b) {
+struct BatchHistLayout {
+  static constexpr int P = KBITS / 8;                 // places of 8-bit digits
+  static constexpr int C = KBITS == 32 ? 32 : 16;     // counter copies (lanes per copy: 32 / C)
+  static constexpr size_t smem_bytes = (size_t)P * kRadix * C * 4;  // 128 KiB
+};
+
+template <int KBITS>
+__global__ void __launch_bounds__(kSegHistThreads, 1) batch_histogram_kernel(BatchArgs b) {
   using K = typename KeyWord<KBITS>::type;
-  constexpr int P = KBITS / 8;
-  __shared__ uint32_t sh[P * kRadix];
+  using BL = BatchHistLayout<KBITS>;
+  constexpr int P = BL::P, C = BL::C;
+  constexpr int PER_VEC = 16 / (int)sizeof(K);  // keys per 16-byte vector
+  extern __shared__ __align__(16) uint32_t sh[];  // [P * 256][C]
   __shared__ uint32_t scan_tmp[kSegHistThreads / 32 + 1];
   __shared__ uint32_t s_last;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
 
+  {
+    uint4* s4 = reinterpret_cast<uint4*>(sh);
+    for (int i = tid; i < P * kRadix * C / 4; i += kSegHistThreads) s4[i] = make_uint4(0, 0, 0, 0);
+  }
   // zero the first pass's status slab on the way (grid-stride, 16-byte stores)
   if (b.clear) {
     uint4* c = reinterpret_cast<uint4*>(b.clear);
@@ -92,81 +120,112 @@ __global__ void __launch_bounds__(kSegHistThreads) batch_histogram_kernel(BatchA
     for (uint64_t i = (uint64_t)blockIdx.x * kSegHistThreads + tid; i < nv; i += (uint64_t)gridDim.x * kSegHistThreads)
       c[i] = make_uint4(0, 0, 0, 0);
   }
-  const uint32_t item = blockIdx.x;
-  if (item >= b.totals[1]) return;
-  const uint32_t seg = b.hist_seg[item];
-  const uint64_t s0 = b.seg_offsets[seg];
-  const uint32_t len = (uint32_t)(b.seg_offsets[seg + 1] - s0);
-  const uint32_t first = b.hist_base[seg];
-  const uint32_t items = b.hist_base[seg + 1] - first;
-  const uint32_t lo = (item - first) * b.hist_chunk;
-  const uint32_t cnt = min(b.hist_chunk, len - lo);
-  const int p = b.num_places;
-
-  for (int i = tid; i < P * kRadix; i += kSegHistThreads) sh[i] = 0;
   __syncthreads();
 
-  const K* keys = static_cast<const K*>(b.keys_in) + s0 + lo;
+  const int p = b.num_places;
   const uint32_t last_mask = (1u << (b.end_bit - (b.begin_bit + 8 * (p - 1)))) - 1u;
-  for (uint32_t j0 = 0; j0 < cnt; j0 += kSegHistThreads * kSegHistKpt) {
-    K k[kSegHistKpt];
-    bool v[kSegHistKpt];
-#pragma unroll
-    for (int u = 0; u < kSegHistKpt; ++u) {
-      const uint32_t j = j0 + u * kSegHistThreads + tid;
-      v[u] = j < cnt;
-      const K raw = v[u] ? __ldcs(keys + j) : K(0);
-      k[u] = b.flip ? flip_to_ordered(raw) : raw;
-    }
+  const bool flip = b.flip != 0;
+  uint32_t* mine = sh + (lane % C);
+  auto count_key = [&](K k) {
+    const K o = flip ? flip_to_ordered(k) : k;
 #pragma unroll
     for (int pl = 0; pl < P; ++pl) {
       if (pl < p) {
-        // merge runs of equal digits among this thread's keys, one atomic per run
-        const int shift = b.begin_bit + 8 * pl;
-        const uint32_t mask = pl == p - 1 ? last_mask : 0xFFu;
-        uint32_t* h = sh + pl * kRadix;
-        uint32_t run_digit = 0, run_len = 0;
-#pragma unroll
-        for (int u = 0; u < kSegHistKpt; ++u) {
-          if (!v[u]) continue;
-          const uint32_t d = digit_of(k[u], shift, mask, pl == p - 1 ? b.top_xor : 0u);
-          if (run_len != 0 && d == run_digit) {
-            ++run_len;
-          } else {
-            if (run_len) atomicAdd(h + run_digit, run_len);
-            run_digit = d;
-            run_len = 1;
-          }
-        }
-        if (run_len) atomicAdd(h + run_digit, run_len);
+        const uint32_t d =
+            digit_of(o, b.begin_bit + 8 * pl, pl == p - 1 ? last_mask : 0xFFu, pl == p - 1 ? b.top_xor : 0u);
+        atomicAdd(mine + (pl * kRadix + d) * C, 1u);
       }
     }
-  }
-  __syncthreads();
-  uint32_t* gh = b.seg_hist + (size_t)seg * p * kRadix;
-  for (int i = tid; i < p * kRadix; i += kSegHistThreads) {
-    const uint32_t c = sh[i];
-    if (c) atomicAdd(gh + i, c);
-  }
+  };
 
-  // the segment's last item: exclusive sum of each place's counts
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(b.seg_done + seg, 1u) == items - 1) ? 1u : 0u;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  uint32_t* go = b.seg_bin_offsets + (size_t)seg * p * kRadix;
-  for (int pl = 0; pl < p; ++pl) {
-    // descending: bins of the complemented digits (count of t = count of t ^ mask)
-    const uint32_t pmask = pl == p - 1 ? last_mask : 0xFFu;
-    const uint32_t src = b.descending ? (tid ^ pmask) : (uint32_t)tid;
-    const uint32_t c = (tid < kRadix && (uint32_t)tid <= pmask) ? ld_relaxed_gpu(gh + pl * kRadix + src) : 0u;
-    const uint32_t excl = block_exclusive_sum<kSegHistThreads>(c, scan_tmp);
-    if (tid < kRadix) go[pl * kRadix + tid] = excl;
-    const int skewed = __syncthreads_or(tid < kRadix && (uint64_t)c * kSkewDivisor > len);
-    if (tid == 0) b.seg_skew[(size_t)seg * p + pl] = skewed ? 1u : 0u;
+  // add this block's copies of every counter into the segment's histograms
+  // (each lane starts at a different copy, so a warp's reads and the zeroing
+  // stores hit distinct banks); the flush that completes the segment's work
+  // items takes its exclusive sums
+  auto flush = [&](uint32_t seg, uint32_t nitems) {
+    __syncthreads();
+    uint32_t* gh = b.seg_hist + (size_t)seg * p * kRadix;
+    for (int e = tid; e < p * kRadix; e += kSegHistThreads) {
+      uint32_t sum = 0;
+#pragma unroll 8
+      for (int c = 0; c < C; ++c) {
+        uint32_t* w = sh + e * C + ((c + lane) % C);
+        sum += *w;
+        *w = 0u;
+      }
+      if (sum) atomicAdd(gh + e, sum);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t items = b.hist_base[seg + 1] - b.hist_base[seg];
+      s_last = (atomicAdd(b.seg_done + seg, nitems) + nitems == items) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      const uint32_t len = (uint32_t)(b.seg_offsets[seg + 1] - b.seg_offsets[seg]);
+      uint32_t* go = b.seg_bin_offsets + (size_t)seg * p * kRadix;
+      for (int pl = 0; pl < p; ++pl) {
+        // descending: bins of the complemented digits (count of t = count of t ^ mask)
+        const uint32_t pmask = pl == p - 1 ? last_mask : 0xFFu;
+        const uint32_t src = b.descending ? (tid ^ pmask) : (uint32_t)tid;
+        const uint32_t c = (tid < kRadix && (uint32_t)tid <= pmask) ? ld_relaxed_gpu(gh + pl * kRadix + src) : 0u;
+        const uint32_t excl = block_exclusive_sum<kSegHistThreads>(c, scan_tmp);
+        if (tid < kRadix) go[pl * kRadix + tid] = excl;
+        const int skewed = __syncthreads_or(tid < kRadix && (uint64_t)c * kSkewDivisor > len);
+        if (tid == 0) b.seg_skew[(size_t)seg * p + pl] = skewed ? 1u : 0u;
+      }
+    }
+    __syncthreads();
+  };
+
+  // this block's contiguous range of work items
+  const uint32_t total_items = b.totals[1];
+  const uint32_t per_block = (total_items + gridDim.x - 1) / gridDim.x;
+  const uint32_t it0 = min(blockIdx.x * per_block, total_items);
+  const uint32_t it1 = min(it0 + per_block, total_items);
+  uint32_t cur = 0xFFFFFFFFu, run = 0;
+  for (uint32_t item = it0; item < it1; ++item) {
+    const uint32_t seg = b.hist_seg[item];
+    if (seg != cur) {
+      if (run) flush(cur, run);
+      cur = seg;
+      run = 0;
+    }
+    const uint64_t s0 = b.seg_offsets[seg];
+    const uint32_t len = (uint32_t)(b.seg_offsets[seg + 1] - s0);
+    const uint32_t lo = (item - b.hist_base[seg]) * b.hist_chunk;
+    const uint32_t cnt = min(b.hist_chunk, len - lo);
+    const K* keys = static_cast<const K*>(b.keys_in) + s0 + lo;
+    // 16-byte vectors between an unaligned head and a tail of fewer than PER_VEC keys
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(keys);
+    uint32_t head = (uint32_t)(((16u - (addr & 15u)) & 15u) / sizeof(K));
+    if (head > cnt) head = cnt;
+    const uint32_t nvec = (cnt - head) / PER_VEC;
+    const uint32_t tail_start = head + nvec * PER_VEC;
+    const uint4* vkeys = reinterpret_cast<const uint4*>(keys + head);
+    for (uint32_t base = 0; base < nvec; base += kSegHistThreads * kSegHistVec) {
+      uint4 v[kSegHistVec];
+#pragma unroll
+      for (int u = 0; u < kSegHistVec; ++u) {
+        const uint32_t idx = base + u * kSegHistThreads + tid;
+        v[u] = idx < nvec ? __ldcs(vkeys + idx) : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < kSegHistVec; ++u) {
+        if (base + u * kSegHistThreads + tid < nvec) {
+          const K* kk = reinterpret_cast<const K*>(&v[u]);
+#pragma unroll
+          for (int j = 0; j < PER_VEC; ++j) count_key(kk[j]);
+        }
+      }
+    }
+    const uint32_t extra = head + (cnt - tail_start);
+    if ((uint32_t)tid < extra) count_key(keys[(uint32_t)tid < head ? tid : tail_start + (tid - head)]);
+    ++run;
   }
+  if (run) flush(cur, run);
 }
 
 // One-block sort of a small segment (up to LocalConfig::T keys).
@@ -303,13 +362,22 @@ cudaError_t launch_batch_plan(const BatchArgs& b, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_histogram(int key_bits, const BatchArgs& b, cudaStream_t s) {
-  const uint32_t grid = b.max_items > 0 ? b.max_items : 1;
-  if (key_bits == 32)
-    batch_histogram_kernel<32><<<grid, kSegHistThreads, 0, s>>>(b);
-  else
-    batch_histogram_kernel<64><<<grid, kSegHistThreads, 0, s>>>(b);
+template <int KBITS>
+cudaError_t launch_batch_histogram_t(const BatchArgs& b, int grid, cudaStream_t s) {
+  constexpr size_t bytes = BatchHistLayout<KBITS>::smem_bytes;
+  // set on every launch: an idempotent host-side attribute
+  cudaError_t e = cudaFuncSetAttribute(batch_histogram_kernel<KBITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)bytes);
+  if (e != cudaSuccess) return e;
+  batch_histogram_kernel<KBITS><<<grid, kSegHistThreads, bytes, s>>>(b);
   return cudaGetLastError();
+}
+
+cudaError_t launch_batch_histogram(int key_bits, const BatchArgs& b, cudaStream_t s) {
+  // one block per SM (128 KiB of shared memory each), at most one per work item
+  const int grid = ws_grid(b.max_items > 0 ? b.max_items : 1u);
+  if (grid <= 0) return cudaErrorInvalidConfiguration;
+  return key_bits == 32 ? launch_batch_histogram_t<32>(b, grid, s) : launch_batch_histogram_t<64>(b, grid, s);
 }
 
 cudaError_t launch_batch_local_sort(int key_bits, bool pairs, const BatchArgs& b, cudaStream_t s) {
