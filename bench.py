@@ -52,6 +52,8 @@ def parse_args():
                    help="other offered loads (fractions of the measured capacity) for the serving stream")
     p.add_argument("--e2e-lanes", type=int, default=3, help="streams (each with a device workspace) the end-to-end calls rotate over")
     p.add_argument("--keys-only", action="store_true", help="sort keys without values")
+    p.add_argument("--host-copy-mode", choices=["default", "engines", "link"], default="default",
+                   help="how the end-to-end host-buffer calls move data (os_set_host_copy_mode)")
     p.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
     p.add_argument("--serve-requests", type=int, default=10000)
     p.add_argument("--no-std-full", action="store_true",
@@ -525,6 +527,8 @@ def main():
         torch.cuda.synchronize()
 
     osw.load()
+    if args.host_copy_mode != "default":
+        osw.os_set_host_copy_mode(osw.OS_HOST_COPY_LINK if args.host_copy_mode == "link" else osw.OS_HOST_COPY_ENGINES)
     n = 1 << args.log2n
     if args.tile_config is not None:
         for vb in (0, 4):
@@ -648,39 +652,56 @@ def main():
             if rc != osw.OS_OK:
                 raise osw.OnesweepError(rc, "sort (host buffers)")
 
-        for i in range(lanes):
-            e2e_step(i)
-        torch.cuda.synchronize(dev)
-        barrier()
-        e0 = [torch.cuda.Event(enable_timing=True) for _ in range(lanes)]
-        e1 = [torch.cuda.Event(enable_timing=True) for _ in range(lanes)]
-        t0 = time.perf_counter()
-        for b in range(lanes):
-            e0[b].record(streams[b])
-        for i in range(args.e2e_steps):
-            e2e_step(i)
-        for b in range(lanes):
-            e1[b].record(streams[b])
-        torch.cuda.synchronize(dev)
-        barrier()
-        wall_ms = (time.perf_counter() - t0) * 1e3
-        et_ms = max(max(e0[a].elapsed_time(e1[b]) for a in range(lanes) for b in range(lanes)), 0.0)
-        et = torch.tensor([max(et_ms, wall_ms)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(et, op=dist.ReduceOp.MAX)
-        for b in range(lanes):
-            st = osw.os_workspace_status(wss[b].data_ptr(), streams[b].cuda_stream)
-            if st != osw.OS_OK:
-                raise osw.OnesweepError(st, "device status after the end-to-end steps")
-        e2e = {"value": world * n * args.e2e_steps / (float(et.item()) / 1e3) / 1e9, "unit": UNIT,
+        def timed_e2e():
+            for i in range(lanes):
+                e2e_step(i)
+            torch.cuda.synchronize(dev)
+            barrier()
+            e0 = [torch.cuda.Event(enable_timing=True) for _ in range(lanes)]
+            e1 = [torch.cuda.Event(enable_timing=True) for _ in range(lanes)]
+            t0 = time.perf_counter()
+            for b in range(lanes):
+                e0[b].record(streams[b])
+            for i in range(args.e2e_steps):
+                e2e_step(i)
+            for b in range(lanes):
+                e1[b].record(streams[b])
+            torch.cuda.synchronize(dev)
+            barrier()
+            wall_ms = (time.perf_counter() - t0) * 1e3
+            et_ms = max(max(e0[a].elapsed_time(e1[b]) for a in range(lanes) for b in range(lanes)), 0.0)
+            et = torch.tensor([max(et_ms, wall_ms)], dtype=torch.float64, device=dev)
+            if world > 1:
+                dist.all_reduce(et, op=dist.ReduceOp.MAX)
+            for b in range(lanes):
+                st = osw.os_workspace_status(wss[b].data_ptr(), streams[b].cuda_stream)
+                if st != osw.OS_OK:
+                    raise osw.OnesweepError(st, "device status after the end-to-end steps")
+            last = (args.e2e_steps - 1) % lanes
+            ok = np.array_equal(hko[last].numpy()[:: 1 << 16], keys_out.cpu().numpy()[:: 1 << 16])
+            if not ok:
+                raise RuntimeError("end-to-end result differs from the device result")
+            return world * n * args.e2e_steps / (float(et.item()) / 1e3) / 1e9
+
+        # the library's default copy mode gives the headline figure; the other
+        # mode (copy kernels over the host link, or the copy engines) is timed
+        # beside it on one GPU
+        mode_names = {osw.OS_HOST_COPY_ENGINES: "copy engines (cudaMemcpyAsync)",
+                      osw.OS_HOST_COPY_LINK: "copy kernels reading and writing the mapped host buffers"}
+        default_mode = osw.os_get_host_copy_mode()
+        e2e = {"value": timed_e2e(), "unit": UNIT,
                "h2d_bytes_per_step": hk.numel() * kbytes + (hv.numel() * 4 if pairs else 0),
                "d2h_bytes_per_step": hk.numel() * kbytes + (hv.numel() * 4 if pairs else 0), "steps": args.e2e_steps,
                "api": "os_sort_pairs_host" if pairs else "os_sort_keys_host",
-               "pipelined": f"calls rotate over {lanes} streams with a device workspace each"}
-        last = (args.e2e_steps - 1) % lanes
-        ok = np.array_equal(hko[last].numpy()[:: 1 << 16], keys_out.cpu().numpy()[:: 1 << 16])
-        if not ok:
-            raise RuntimeError("end-to-end result differs from the device result")
+               "pipelined": f"calls rotate over {lanes} streams with a device workspace each",
+               "copies": mode_names[default_mode]}
+        if world == 1 and not args.no_extras:
+            other = osw.OS_HOST_COPY_LINK if default_mode == osw.OS_HOST_COPY_ENGINES else osw.OS_HOST_COPY_ENGINES
+            osw.os_set_host_copy_mode(other)
+            try:
+                e2e["other_copy_mode"] = {"copies": mode_names[other], "value": timed_e2e()}
+            finally:
+                osw.os_set_host_copy_mode(default_mode)
 
     batched = serving = configs = copy_ceiling = digit_widths = None
     if world == 1 and not args.no_extras:

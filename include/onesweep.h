@@ -159,6 +159,23 @@ OS_API int os_sort_pairs_host(int key_type, const void *keys_in, void *keys_out,
                               void *stream);
 
 /*
+ * How the host-memory sorts above move data between host and device memory
+ * (process-wide; not part of the paper). OS_HOST_COPY_ENGINES (the default):
+ * cudaMemcpyAsync on the call's stream. OS_HOST_COPY_LINK: copy kernels on the
+ * call's stream that read or write the host buffers directly through their
+ * device mapping - page-locked buffers only (cudaHostAlloc, or cudaHostRegister
+ * with cudaHostRegisterMapped) that start 16-byte aligned (the last bytes of
+ * a count that is not a multiple of 16 still go through the copy engines);
+ * any other buffer takes the copy engines. Results are the same in both
+ * modes. os_set_host_copy_mode returns OS_OK, or OS_ERR_INVALID_ARG for an
+ * unknown mode; os_get_host_copy_mode returns the mode in force.
+ */
+#define OS_HOST_COPY_ENGINES 0
+#define OS_HOST_COPY_LINK 1
+OS_API int os_set_host_copy_mode(int mode);
+OS_API int os_get_host_copy_mode(void);
+
+/*
  * Segmented (batched) sort: num_segments independent arrays held back to
  * back, segment s = [seg_offsets[s], seg_offsets[s+1]), each sorted on its
  * own, in one call of a few launches whatever the number of segments (each

@@ -4,12 +4,92 @@
 // Section 3 on those buffers, and the download of the result into the host
 // output buffers. The workspace starts with the device sort's own workspace
 // (so os_workspace_status reads it as usual), followed by the staging buffers.
+//
+// The copies between host and device memory run either on the copy engines
+// (cudaMemcpyAsync) or, in the host-link mode, as kernels that read or write
+// the page-locked host buffers directly through their device mapping (on
+// GB300 the host memory sits across the NVLink-C2C link). The mode is a
+// process-wide setting; buffers that are pageable, unmapped or not 16-byte
+// aligned always take the copy engines.
 #include <cuda_runtime.h>
+
+#include <atomic>
 
 #include "../../include/onesweep.h"
 #include "os_internal.h"
 
 namespace {
+
+std::atomic<int> g_host_copy_mode{OS_HOST_COPY_ENGINES};
+
+// Copy of nvec 16-byte words between device memory and mapped host memory
+// (either side may be host memory). Small blocks of at most 32 registers a
+// thread, so one fits on an SM beside three binning blocks (which hold
+// 61 440 of its 65 536 registers) while another call's sort runs; kLinkUnroll
+// loads in flight per thread, and up to 4 blocks per SM, cover the link's
+// latency.
+constexpr int kLinkThreads = 128;
+constexpr int kLinkUnroll = 4;
+
+__global__ void __launch_bounds__(kLinkThreads, 16) link_copy_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst,
+                                                                 size_t nvec) {
+  const size_t step = (size_t)kLinkThreads * kLinkUnroll;
+  for (size_t base = (size_t)blockIdx.x * step + threadIdx.x; base < nvec; base += (size_t)gridDim.x * step) {
+    uint4 v[kLinkUnroll];
+#pragma unroll
+    for (int u = 0; u < kLinkUnroll; ++u) {
+      const size_t i = base + (size_t)u * kLinkThreads;
+      if (i < nvec) v[u] = __ldcs(src + i);
+    }
+#pragma unroll
+    for (int u = 0; u < kLinkUnroll; ++u) {
+      const size_t i = base + (size_t)u * kLinkThreads;
+      if (i < nvec) __stcs(dst + i, v[u]);
+    }
+  }
+}
+
+// Device address of a page-locked, mapped host buffer (null otherwise).
+void* mapped_host(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// One host<->device copy: in the host-link mode, when the host side is
+// mapped and both sides start 16-byte aligned, the kernel copies the whole
+// 16-byte words and the copy engines the last bytes (fewer than 16); the copy
+// engines copy everything otherwise.
+cudaError_t copy_async(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s) {
+  if (bytes == 0) return cudaSuccess;
+  if (g_host_copy_mode.load(std::memory_order_relaxed) == OS_HOST_COPY_LINK && bytes >= 16) {
+    const void* host = kind == cudaMemcpyHostToDevice ? src : dst;
+    void* mapped = mapped_host(host);
+    const void* from = kind == cudaMemcpyHostToDevice ? mapped : src;
+    void* to = kind == cudaMemcpyHostToDevice ? dst : mapped;
+    if (mapped && reinterpret_cast<uintptr_t>(from) % 16 == 0 && reinterpret_cast<uintptr_t>(to) % 16 == 0) {
+      const size_t nvec = bytes / 16;
+      int sms = 0, dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        return cudaErrorInvalidValue;
+      const size_t per_block = (size_t)kLinkThreads * kLinkUnroll;
+      size_t grid = (nvec + per_block - 1) / per_block;
+      if (grid > (size_t)sms * 4) grid = (size_t)sms * 4;
+      link_copy_kernel<<<(unsigned)grid, kLinkThreads, 0, s>>>(static_cast<const uint4*>(from),
+                                                              static_cast<uint4*>(to), nvec);
+      const cudaError_t e = cudaGetLastError();
+      const size_t done = nvec * 16;
+      if (e != cudaSuccess || done == bytes) return e;
+      return cudaMemcpyAsync(static_cast<char*>(dst) + done, static_cast<const char*>(src) + done, bytes - done,
+                             kind, s);
+    }
+  }
+  return cudaMemcpyAsync(dst, src, bytes, kind, s);
+}
 
 constexpr size_t kAlign = 256;
 size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -90,14 +170,14 @@ int sort_host(int key_type, const void* keys_in, void* keys_out, const uint32_t*
   void* d_keys_out = w + L.keys_out;
   uint32_t* d_vals_in = pairs ? reinterpret_cast<uint32_t*>(w + L.vals_in) : nullptr;
   uint32_t* d_vals_out = pairs ? reinterpret_cast<uint32_t*>(w + L.vals_out) : nullptr;
-  if (cudaMemcpyAsync(d_keys_in, keys_in, kbytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return OS_ERR_CUDA;
-  if (pairs && cudaMemcpyAsync(d_vals_in, vals_in, vbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+  if (copy_async(d_keys_in, keys_in, kbytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return OS_ERR_CUDA;
+  if (pairs && copy_async(d_vals_in, vals_in, vbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return OS_ERR_CUDA;
   const int rc = onesweep::sort_on_workspace(key_type, d_keys_in, d_keys_out, d_vals_in, d_vals_out, n, begin_bit,
                                              end_bit, ws, L.sort_bytes, stream);
   if (rc != OS_OK) return rc;
-  if (cudaMemcpyAsync(keys_out, d_keys_out, kbytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return OS_ERR_CUDA;
-  if (pairs && cudaMemcpyAsync(vals_out, d_vals_out, vbytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+  if (copy_async(keys_out, d_keys_out, kbytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return OS_ERR_CUDA;
+  if (pairs && copy_async(vals_out, d_vals_out, vbytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return OS_ERR_CUDA;
   return OS_OK;
 }
@@ -115,6 +195,14 @@ OS_API int os_sort_keys_host(int key_type, const void* keys_in, void* keys_out, 
                              int end_bit, void* ws, size_t ws_bytes, void* stream) {
   return sort_host(key_type, keys_in, keys_out, nullptr, nullptr, n, begin_bit, end_bit, ws, ws_bytes, stream);
 }
+
+OS_API int os_set_host_copy_mode(int mode) {
+  if (mode != OS_HOST_COPY_ENGINES && mode != OS_HOST_COPY_LINK) return OS_ERR_INVALID_ARG;
+  g_host_copy_mode.store(mode, std::memory_order_relaxed);
+  return OS_OK;
+}
+
+OS_API int os_get_host_copy_mode(void) { return g_host_copy_mode.load(std::memory_order_relaxed); }
 
 OS_API int os_sort_pairs_host(int key_type, const void* keys_in, void* keys_out, const uint32_t* vals_in,
                               uint32_t* vals_out, uint64_t n, int begin_bit, int end_bit, void* ws, size_t ws_bytes,

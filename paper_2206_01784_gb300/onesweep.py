@@ -23,6 +23,7 @@ KEY_BITS = {OS_KEY_U32: 32, OS_KEY_U64: 64, OS_KEY_F32: 32, OS_KEY_F64: 64, OS_K
 
 OS_OK, OS_ERR_INVALID_ARG, OS_ERR_TOO_LARGE, OS_ERR_WORKSPACE, OS_ERR_CUDA, OS_ERR_TIMEOUT = range(6)
 OS_ERR_SCRATCH_LIMIT = 6
+OS_HOST_COPY_ENGINES, OS_HOST_COPY_LINK = 0, 1  # how the host-memory sorts move data
 
 
 class OnesweepError(RuntimeError):
@@ -109,6 +110,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.os_sort_keys_host.argtypes = [i32, vp, vp, u64, i32, i32, vp, sz, vp]
     lib.os_sort_pairs_host.restype = i32
     lib.os_sort_pairs_host.argtypes = [i32, vp, vp, vp, vp, u64, i32, i32, vp, sz, vp]
+    lib.os_set_host_copy_mode.restype = i32
+    lib.os_set_host_copy_mode.argtypes = [i32]
+    lib.os_get_host_copy_mode.restype = i32
+    lib.os_get_host_copy_mode.argtypes = []
     lib.os_num_tile_configs.restype = i32
     lib.os_num_tile_configs.argtypes = []
     lib.os_tile_config_keys.restype = i32
@@ -254,6 +259,14 @@ def os_sort_pairs_host(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_
                        stream) -> int:
     return int(load().os_sort_pairs_host(key_type, keys_in, keys_out, vals_in, vals_out, n, begin_bit, end_bit, ws,
                                          ws_bytes, stream))
+
+
+def os_set_host_copy_mode(mode: int) -> int:
+    return int(load().os_set_host_copy_mode(mode))
+
+
+def os_get_host_copy_mode() -> int:
+    return int(load().os_get_host_copy_mode())
 
 
 def os_build_info() -> str:

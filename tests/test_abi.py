@@ -204,3 +204,18 @@ def test_noalloc_scratch_covers_2_20_keys():
         bits = 64 if name in ("u64", "f64", "i64") else 32
         for vb in (0, 4):
             assert 0 < osw.os_sort_workspace_bytes(kt, 1 << 20, vb, 0, bits) <= 16 << 20, (name, vb)
+
+
+def test_host_copy_mode_setting():
+    # a process-wide setting read by the host-memory sorts; no GPU needed
+    old = osw.os_get_host_copy_mode()
+    assert old in (osw.OS_HOST_COPY_ENGINES, osw.OS_HOST_COPY_LINK)
+    try:
+        assert osw.os_set_host_copy_mode(osw.OS_HOST_COPY_LINK) == osw.OS_OK
+        assert osw.os_get_host_copy_mode() == osw.OS_HOST_COPY_LINK
+        assert osw.os_set_host_copy_mode(7) == osw.OS_ERR_INVALID_ARG
+        assert osw.os_get_host_copy_mode() == osw.OS_HOST_COPY_LINK
+        assert osw.os_set_host_copy_mode(osw.OS_HOST_COPY_ENGINES) == osw.OS_OK
+        assert osw.os_get_host_copy_mode() == osw.OS_HOST_COPY_ENGINES
+    finally:
+        osw.os_set_host_copy_mode(old)

@@ -76,11 +76,25 @@ def _run(kt, keys, vals, begin, end, pinned, stream=None):
     return ko if vals is None else (ko, _as_np(hvo, np.uint32).copy())
 
 
+@pytest.fixture(params=["engines", "link"])
+def copy_mode(request):
+    """Both ways the host-memory sorts move data: the copy engines and the
+    copy kernels over the host link (page-locked buffers only; others fall
+    back to the copy engines)."""
+    mode = {"engines": osw.OS_HOST_COPY_ENGINES, "link": osw.OS_HOST_COPY_LINK}[request.param]
+    old = osw.os_get_host_copy_mode()
+    assert osw.os_set_host_copy_mode(mode) == osw.OS_OK
+    yield mode
+    osw.os_set_host_copy_mode(old)
+
+
 @pytest.mark.parametrize("pinned", [True, False])
 @pytest.mark.parametrize("kt,pairs,begin,end", [("u32", True, 0, 32), ("u32", False, 0, 32), ("u64", True, 0, 64),
                                                  ("f32", True, 0, 32), ("i64", True, 3, 64), ("f64", False, 0, 64)])
-def test_host_sort_exact(kt, pairs, begin, end, pinned):
-    n = 300_007
+@pytest.mark.parametrize("n", [300_007, 300_008])
+def test_host_sort_exact(kt, pairs, begin, end, pinned, copy_mode, n):
+    # 300 008 keys: byte counts that are multiples of 16 (the link copy kernel
+    # alone); 300 007: the kernel and a tail through the copy engines
     keys = _keys(kt, n, seed=31)
     vals = workload.iota_u32(n) if pairs else None
     got = _run(kt, keys, vals, begin, end, pinned)
@@ -91,7 +105,7 @@ def test_host_sort_exact(kt, pairs, begin, end, pinned):
         assert np.array_equal(got, exp)
 
 
-def test_host_sort_two_streams():
+def test_host_sort_two_streams(copy_mode):
     dev = _dev()
     n = 1 << 20
     ks = [_keys("u32", n, seed=40 + i) for i in range(2)]
@@ -136,3 +150,32 @@ def test_binding_sort_host_numpy(kt, pairs):
         assert np.array_equal(got[0].view(exp[0].dtype), exp[0]) and np.array_equal(got[1].view(np.uint32), exp[1])
     else:
         assert np.array_equal(got.view(exp.dtype), exp)
+
+
+@pytest.mark.parametrize("offset,n", [(0, 4100), (0, 4099), (0, 3), (1, 4100), (4, 4100), (3, 70001)])
+def test_host_link_mode_unaligned_and_odd_sizes(offset, n, copy_mode):
+    # in the link mode, host buffers that start off a 16-byte boundary (offsets
+    # 1 and 3 words) take the copy engines; aligned ones (offsets 0 and 4
+    # words) the copy kernel, plus the copy engines for a tail of fewer than
+    # 16 bytes (n = 4099) or for a buffer of fewer than 16 bytes (n = 3):
+    # every case bit-exact
+    dev = _dev()
+    keys = _keys("u32", n, seed=61 + offset + n)
+    vals = workload.iota_u32(n)
+    pad = torch.empty(n + 8, dtype=torch.int32).pin_memory()
+    padv = torch.empty(n + 8, dtype=torch.int32).pin_memory()
+    hk, hv = pad[offset:offset + n], padv[offset:offset + n]
+    hk.copy_(torch.from_numpy(keys.view(np.int32)))
+    hv.copy_(torch.from_numpy(vals.view(np.int32)))
+    hko = torch.empty(n + 8, dtype=torch.int32).pin_memory()[offset:offset + n]
+    hvo = torch.empty(n + 8, dtype=torch.int32).pin_memory()[offset:offset + n]
+    wsb = osw.os_sort_host_workspace_bytes(osw.OS_KEY_U32, n, 4, 0, 32)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream().cuda_stream
+    rc = osw.os_sort_pairs_host(osw.OS_KEY_U32, hk.data_ptr(), hko.data_ptr(), hv.data_ptr(), hvo.data_ptr(), n, 0,
+                                32, ws.data_ptr(), wsb, s)
+    assert rc == osw.OS_OK
+    assert osw.os_workspace_status(ws.data_ptr(), s) == osw.OS_OK
+    exp = oracle.sort("u32", keys, vals, 0, 32)
+    assert np.array_equal(hko.numpy().view(np.uint32), exp[0])
+    assert np.array_equal(hvo.numpy().view(np.uint32), exp[1])
