@@ -163,8 +163,9 @@ OS_API int os_sort_pairs_host(int key_type, const void *keys_in, void *keys_out,
  * (process-wide; not part of the paper). OS_HOST_COPY_ENGINES (the default):
  * cudaMemcpyAsync on the call's stream. OS_HOST_COPY_LINK: copy kernels on the
  * call's stream that read or write the host buffers directly through their
- * device mapping - page-locked buffers only (cudaHostAlloc, or cudaHostRegister
- * with cudaHostRegisterMapped) that start 16-byte aligned (the last bytes of
+ * device mapping - host ranges that are page-locked and mapped from their
+ * first to their last byte (cudaHostAlloc, or cudaHostRegister with
+ * cudaHostRegisterMapped) and start 16-byte aligned (the last bytes of
  * a count that is not a multiple of 16 still go through the copy engines);
  * any other buffer takes the copy engines. Results are the same in both
  * modes. os_set_host_copy_mode returns OS_OK, or OS_ERR_INVALID_ARG for an

@@ -49,14 +49,24 @@ __global__ void __launch_bounds__(kLinkThreads, 16) link_copy_kernel(const uint4
   }
 }
 
-// Device address of a page-locked, mapped host buffer (null otherwise).
-void* mapped_host(const void* p) {
+// Device address of a page-locked, mapped host byte (null otherwise).
+void* mapped_host_byte(const void* p) {
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     (void)cudaGetLastError();
     return nullptr;
   }
   return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// Device address of a host range whose first and last bytes are both
+// page-locked and mapped at device addresses `bytes - 1` apart (null
+// otherwise: a range only partly page-locked takes the copy engines).
+void* mapped_host(const void* p, size_t bytes) {
+  char* first = static_cast<char*>(mapped_host_byte(p));
+  if (!first) return nullptr;
+  char* last = static_cast<char*>(mapped_host_byte(static_cast<const char*>(p) + bytes - 1));
+  return last == first + (bytes - 1) ? first : nullptr;
 }
 
 // One host<->device copy: in the host-link mode, when the host side is
@@ -67,7 +77,7 @@ cudaError_t copy_async(void* dst, const void* src, size_t bytes, cudaMemcpyKind 
   if (bytes == 0) return cudaSuccess;
   if (g_host_copy_mode.load(std::memory_order_relaxed) == OS_HOST_COPY_LINK && bytes >= 16) {
     const void* host = kind == cudaMemcpyHostToDevice ? src : dst;
-    void* mapped = mapped_host(host);
+    void* mapped = mapped_host(host, bytes);
     const void* from = kind == cudaMemcpyHostToDevice ? mapped : src;
     void* to = kind == cudaMemcpyHostToDevice ? dst : mapped;
     if (mapped && reinterpret_cast<uintptr_t>(from) % 16 == 0 && reinterpret_cast<uintptr_t>(to) % 16 == 0) {
