@@ -157,3 +157,127 @@ def test_a_wrong_span_is_caught():
     finally:
         _steps = good
     assert finals != {tuple((G, int(v)) for v in np.cumsum([1, 2, 3, 4]))}
+
+
+# ---------------------------------------------------------------------------
+# The kernel's own round structure: a round issues reads of up to W preceding
+# counters (each read is its own atomic step, so the reads of one round may
+# see different moments), then folds them in order exactly as the kernel's
+# consume() does - stop at an N, after an aggregate skip the window's
+# remaining rows - and publishes an aggregate after a round that moved, or G
+# once done. Checked: every terminal state holds the inclusive prefixes, and a
+# terminal state stays reachable from every reachable state (no livelock).
+
+W = 4
+
+
+def _kernel_steps(counts, counters, progs):
+    out = []
+    for t, prog in enumerate(progs):
+        kind = prog[0]
+        if kind == "done":
+            continue
+        c = list(counters)
+        p = list(progs)
+        if kind == "pub_l":
+            c[t] = (G, counts[t], 1) if t == 0 else (L, counts[t], 1)
+            p[t] = ("done",) if t == 0 else ("read", t, 0, ())
+        elif kind == "read":
+            _, left, exclusive, got = prog
+            w = len(got)
+            # rows before the chain's first tile read as (G, 0), as in issue()
+            val = counters[left - 1 - w] if w < left else (G, 0, 1)
+            got = got + (val,)
+            if len(got) < W:
+                p[t] = ("read", left, exclusive, got)
+            else:
+                left0, done = left, False
+                for s, v, span in got:
+                    if done or s == N:
+                        break
+                    if s == A:
+                        exclusive += v
+                        left -= span
+                        done = left == 0
+                        break
+                    exclusive += v
+                    left -= 1
+                    done = s == G or left == 0
+                if done:
+                    p[t] = ("pub_g", exclusive + counts[t])
+                elif left != left0 and t - left + 1 <= MAX_SPAN:
+                    p[t] = ("pub_a", left, exclusive)
+                else:
+                    p[t] = ("read", left, exclusive, ())
+        elif kind == "pub_a":
+            _, left, exclusive = prog
+            c[t] = (A, exclusive + counts[t], t - left + 1)
+            p[t] = ("read", left, exclusive, ())
+        elif kind == "pub_g":
+            c[t] = (G, prog[1], 1)
+            p[t] = ("done",)
+        out.append((tuple(c), tuple(p)))
+    return out
+
+
+def _explore_kernel(counts):
+    g = len(counts)
+    start = (tuple((N, 0, 1) for _ in range(g)), tuple(("pub_l",) for _ in range(g)))
+    succ = {}
+    stack = [start]
+    while stack:
+        st = stack.pop()
+        if st in succ:
+            continue
+        nxt = _kernel_steps(counts, *st)
+        succ[st] = nxt
+        stack.extend(n for n in nxt if n not in succ)
+    terminal = {s for s, n in succ.items() if not n}
+    # states from which a terminal state is reachable (reverse reachability)
+    pred = {s: [] for s in succ}
+    for s, n in succ.items():
+        for x in n:
+            pred[x].append(s)
+    good, work = set(terminal), list(terminal)
+    while work:
+        x = work.pop()
+        for y in pred[x]:
+            if y not in good:
+                good.add(y)
+                work.append(y)
+    finals = {tuple((s, v) for s, v, _ in st[0]) for st in terminal}
+    return finals, len(good) == len(succ), len(succ)
+
+
+@pytest.mark.parametrize("counts", [(5,), (2, 3), (1, 0, 4), (3, 1, 2, 6), (0, 7, 0, 2)])
+def test_kernel_rounds_every_interleaving(counts):
+    finals, live, states = _explore_kernel(list(counts))
+    assert live, "a reachable state cannot finish"
+    assert finals == {tuple((G, int(v)) for v in np.cumsum(counts))}
+    assert states > len(counts)
+
+
+def test_kernel_rounds_fold_a_stale_window_correctly():
+    # a round whose first row is an aggregate skips the rows read after it,
+    # whatever they held when read: a wrong skip (one row too few) is caught
+    global _kernel_steps
+    good = _kernel_steps
+
+    def skip_one_short(counts, counters, progs):
+        out = []
+        for c, p in good(counts, counters, progs):
+            p = list(p)
+            for t, (old, new) in enumerate(zip(progs, p)):
+                if old[0] == "read" and len(old[3]) == W - 1 and new[0] in ("read", "pub_a"):
+                    got = old[3] + (counters[old[1] - 1 - (W - 1)] if W - 1 < old[1] else (G, 0, 1),)
+                    if got[0][0] == A and new[1] < old[1] - 1:
+                        p[t] = (new[0], new[1] + 1) + tuple(new[2:])
+            out.append((c, tuple(p)))
+        return out
+
+    try:
+        _kernel_steps = skip_one_short
+        finals, _, _ = _explore_kernel([1, 2, 3, 4])
+    finally:
+        _kernel_steps = good
+    assert finals != {tuple((G, int(v)) for v in np.cumsum([1, 2, 3, 4]))}
